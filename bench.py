@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the PRGD hot path on one GB300.
+
+Workload: the orthogonal-cubic tensor-completion problem, order 3, 200 per
+mode, TT-ranks (1,5,5,1), 5% of entries observed (|Omega| = 400 000),
+noiseless; synthetic, seeded.  A step is one PRGD iteration (sampled pass over
+Omega, weights, weighted tangent projection, rank-2r assembly, TT-rounding
+retraction) in the MIXED mode (FP32 sampled pass, FP64 dense stages), with all
+inputs resident in device memory.  L2 is flushed (256 MB write) between timed
+steps, outside the timed brackets.
+
+Prints ONE JSON line.  `--impl reference` times the FP64 CPU oracle on the
+same workload instead (the reference arm; rank 0 only).
+
+Multi-GPU: one process per GPU (torchrun), each solving its own replica
+(seed = rank); value = entries of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Ω-entries/s & PRGD iters/s to rel.err≤1e-6 vs FP64 GPU; p50/p99 solve ms"
+WORKLOAD = {"workload": "orthogonal_cubic", "d": 3, "n": 200, "ranks": [1, 5, 5, 1], "omega": 400000,
+            "frac": 0.05, "noise": 0.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ttc", choices=["ttc", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-solves", type=int, default=3)
+    ap.add_argument("--e2e-iters", type=int, default=20)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline); runs in a fresh process
+# with one BLAS/OpenMP thread so `cores` is what it actually used.
+# ---------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+import oracle as o
+from paper_2501_13385_gb300 import workloads as w
+P = w.orthogonal_cubic(%(seed)d)
+cur = P.init
+times = []
+t_end = time.perf_counter() + %(budget)f
+for i in range(%(warm)d + %(steps)d):
+    t0 = time.perf_counter()
+    cur, _ = o.prgd_step(cur, P.idx, P.y, P.n, P.r, eps_rel=1.0, alpha_scale=1.5)
+    dt = time.perf_counter() - t0
+    if i >= %(warm)d:
+        times.append(dt)
+    if %(bounded)d and i >= %(warm)d + 2 and time.perf_counter() > t_end:
+        break
+print(json.dumps({"N": P.N, "times": times}))
+"""
+
+
+def run_oracle(seed, warm, steps, budget_s, bounded):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = "1"
+    code = ORACLE_SNIPPET % {"root": ROOT, "seed": seed, "warm": warm, "steps": steps, "budget": budget_s,
+                             "bounded": 1 if bounded else 0}
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    res = run_oracle(seed=0, warm=min(args.warmup, 1), steps=args.steps, budget_s=120.0, bounded=True)
+    t = res["times"]
+    ms = 1e3 * statistics.mean(t)
+    value = res["N"] / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Ω-entries/s", "n_gpus": args.gpus,
+        "steps": len(t), "warmup": min(args.warmup, 1), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, precision="fp64", parallelism="rank 0 only (CPU)"),
+        "iters_per_s": 1e3 / ms,
+        "cpu_baseline": {"value": value, "unit": "Ω-entries/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(t)} PRGD iterations of the full workload (oracle, 1 thread)"},
+        "e2e": {"value": value, "unit": "Ω-entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_bytes_per_launch(P, W=1):
+    """Bytes the sampled pass must move per launch: for every mode k, every
+    entry's packed code (4W bytes) and FP32 value (4 bytes), plus one FP32
+    partial (1 + r_k r_{k+1} values) written per chunk of 128 entries."""
+    import numpy as np
+    total = 0
+    for k in range(P.m):
+        counts = np.bincount(P.idx[:, k], minlength=P.n[k])
+        chunks = int(np.sum((counts + 127) // 128))
+        total += P.N * (4 * W + 4) + chunks * (1 + P.r[k] * P.r[k + 1]) * 4
+    return total
+
+
+def load_traffic(kernel_file):
+    """dram bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+        src = open(kernel_file, "rb").read()
+        if rec.get("source_sha1") == hashlib.sha1(src).hexdigest() and rec.get("workload") == WORKLOAD["workload"]:
+            return rec.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def ttc_arm(args):
+    rank, world, local = dist_env()
+    if world > 1:
+        os.environ.setdefault("CUDA_VISIBLE_DEVICES", str(local))
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2501_13385_gb300 import build, ttc
+    from paper_2501_13385_gb300 import workloads as w
+
+    if world > 1:
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    build.build()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    P = w.orthogonal_cubic(rank)
+    ctx = ttc.Context(P.n, P.r, stream=stream.cuda_stream, precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_NONE)
+    ctx.set_observations(P.idx, P.y)
+    ctx.set_cores(P.init)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        ctx.step_async()
+    torch.cuda.synchronize()
+    ctx.profile_enable(True)
+    ctx.step_async()                      # first profiled iteration recaptures the graph
+    torch.cuda.synchronize()
+    ctx.profile_read(reset=True)
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    launches0 = ctx.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(K):
+            ev[i][0].record(stream)
+            ctx.step_async()
+            ev[i][1].record(stream)
+            flush.zero_()
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = ctx.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    kern_ms, kern_n = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / K
+    value = world * P.N * K / (total_ms / 1e3)
+
+    # iterations to rel.err <= 1e-6 (vs T*), mixed and plain FP64, and their time
+    to_tol = {}
+    for name, prec in (("mixed", ttc.PREC_MIXED), ("fp64", ttc.PREC_FP64)):
+        with ttc.Context(P.n, P.r, stream=stream.cuda_stream, precision=prec, stop_rule=ttc.STOP_RELERR,
+                         tol=1e-6, max_iter=200) as c2:
+            c2.set_observations(P.idx, P.y)
+            c2.set_cores(P.init)
+            c2.set_truth(P.truth)
+            res = c2.solve()
+        iters = res["iters"]
+        with ttc.Context(P.n, P.r, stream=stream.cuda_stream, precision=prec, stop_rule=ttc.STOP_NONE,
+                         max_iter=iters) as c3:
+            c3.set_observations(P.idx, P.y)
+            c3.set_cores(P.init)
+            c3.step_async()
+            torch.cuda.synchronize()
+            c3.set_cores(P.init)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c3.solve()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+        to_tol[name] = {"iters": iters, "converged": res["converged"], "ms": 1e3 * dt,
+                        "polish_iter": res["polish_iter"]}
+
+    # end to end through the public API from pinned host buffers
+    idx_h = torch.from_numpy(np.ascontiguousarray(P.idx, dtype=np.int32)).pin_memory().numpy()
+    y_h = torch.from_numpy(np.ascontiguousarray(P.y)).pin_memory().numpy()
+    init_h = [torch.from_numpy(np.ascontiguousarray(c)).pin_memory().numpy() for c in P.init]
+    e2e_ms = []
+    out_bytes = 0
+    with ttc.Context(P.n, P.r, stream=stream.cuda_stream, precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_NONE,
+                     max_iter=args.e2e_iters) as ce:
+        ce.set_observations(idx_h, y_h)       # warm-up call (graph capture, allocations)
+        ce.set_cores(init_h)
+        ce.solve()
+        for _ in range(args.e2e_solves):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ce.set_observations(idx_h, y_h)
+            ce.set_cores(init_h)
+            ce.solve()
+            res_cores = ce.get_cores()
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+            out_bytes = sum(c.nbytes for c in res_cores)
+    h2d = idx_h.nbytes + y_h.nbytes + sum(c.nbytes for c in init_h)
+    e2e_val = world * P.N * args.e2e_iters / (statistics.mean(e2e_ms) / 1e3)
+
+    # roofline of the dominant kernel (the sampled pass)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    alg = algorithmic_bytes_per_launch(P)
+    kern_avg_ms = kern_ms / max(kern_n, 1)
+    achieved = alg / (kern_avg_ms / 1e3) / 1e9
+    traffic = load_traffic(os.path.join(ROOT, "paper_2501_13385_gb300", "csrc", "omega_pass.cu"))
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_sample_project<float,8>", "kernel_ms": kern_avg_ms,
+            "launches_timed": kern_n, "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = run_oracle(seed=0, warm=1, steps=100, budget_s=15.0, bounded=True)
+        t = r["times"]
+        cpu = {"value": r["N"] / statistics.mean(t), "unit": "Ω-entries/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(t)} PRGD iterations of the full workload, ~15 s of one host core"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Ω-entries/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 sampled pass + f64 dense stages", "data": "synthetic",
+            "config": dict(WORKLOAD, precision="mixed", l2="flushed between timed steps (256 MB write)",
+                           parallelism="replicas" if world > 1 else "single GPU"),
+            "iters_per_s": 1e3 / ms_per_step,
+            "step_ms_p50": statistics.median(step_ms), "step_ms_p99": sorted(step_ms)[max(0, int(0.99 * K) - 1)],
+            "to_rel_err_1e-6": to_tol,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "Ω-entries/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": out_bytes, "iters_per_solve": args.e2e_iters,
+                    "ms_per_solve": statistics.mean(e2e_ms)},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ttc_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

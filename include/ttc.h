@@ -1,0 +1,189 @@
+/*
+ * ttc.h - C ABI of a GB300 (sm_103a) library for low-TT-rank tensor
+ * completion by Preconditioned Riemannian Gradient Descent (PRGD).
+ *
+ * Problem (Eq. (model: Low TT)): given mode sizes n_1..n_d, TT-ranks
+ * r_0..r_d (r_0 = r_d = 1), an index set Omega and observed values y,
+ * minimise f(T) = 1/2 ||P_Omega(T - T*)||_F^2 over tensors of TT-rank r.
+ * One iteration is Algorithm 2 (Trim skipped, which Section 3.2 allows):
+ *   G_l = P_Omega(T_l - T*);  G_{l,i} = eps I + diag(M_i(G_l) M_i(G_l)^T);
+ *   W_l = T_l - alpha_l tilde P_T W^{-1} G_l   (Lemma 3.5 closed form);
+ *   T_{l+1} = SVD^tt_r(W_l)                      (Algorithm 1 by TT-rounding).
+ *
+ * Conventions shared by every call:
+ *   - indices are 0-based; `idx` is row-major N x d (entry e, mode k at
+ *     idx[e*d + k]);
+ *   - host core k is a row-major array of shape r[k] x n[k] x r[k+1], the
+ *     paper's T_k in R^{r_{k-1} x d_k x r_k} (Section 2, Eq. (TT Core));
+ *   - every pointer argument is a HOST pointer unless its name ends in
+ *     `_dev`; inputs are copied, outputs go to caller-allocated buffers;
+ *   - a context owns its device memory and its CUDA stream use; it is not
+ *     thread-safe.  Every call returns a ttc_status (0 = success) and never
+ *     exits or throws across the ABI.
+ */
+#ifndef TTC_H
+#define TTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ttc_ctx ttc_ctx;
+
+typedef enum {
+  TTC_OK = 0,
+  TTC_EINVAL = -1,      /* bad argument (sizes, ranks, null pointers, order of calls) */
+  TTC_ENOMEM = -2,      /* device or host allocation failed */
+  TTC_ERANGE = -3,      /* an index coordinate is negative or >= n_k */
+  TTC_EDUP = -4,        /* Omega holds the same index twice (Omega is a set) */
+  TTC_ENONFINITE = -5,  /* NaN/Inf in the input values or during an iteration */
+  TTC_ENOTCONV = -6,    /* ttc_solve hit max_iter before its tolerance */
+  TTC_ETIMEOUT = -7,
+  TTC_ECUDA = -8,       /* a CUDA runtime call failed; see ttc_last_cuda_error */
+  TTC_EBUSY = -9,
+  TTC_EUNSUPPORTED = -10 /* shape outside the compiled limits (order <= 16, rank <= 32) */
+} ttc_status;
+
+/* Precision modes. */
+enum {
+  TTC_PREC_FP64 = 0,   /* every stage in FP64 */
+  TTC_PREC_MIXED = 1,  /* FP32 Omega pass (FP32 accumulate); FP64 dense stages;
+                          ttc_solve switches the pass to FP64 once the relative
+                          residual ||P_Omega(T_l - T*)|| / ||y|| falls below
+                          `polish_below` */
+  TTC_PREC_FP32 = 2    /* FP32 Omega pass only, never polished */
+};
+
+/* Stop rules of ttc_solve. */
+enum {
+  TTC_STOP_RELERR = 0, /* ||T_l - T*||_F / ||T*||_F <= tol (needs ttc_set_truth) */
+  TTC_STOP_STEP = 1,   /* ||T_{l+1} - T_l||_F <= tol * max(1, ||T_l||_F) (Section 5, noise experiment) */
+  TTC_STOP_NONE = 2    /* run exactly max_iter iterations */
+};
+
+typedef struct {
+  int precision;        /* TTC_PREC_* */
+  double eps_rel;       /* eps_l = eps_rel * ||G_l||_F^2 / min_k n_k (reading of Section 3.2) */
+  double alpha_scale;   /* alpha_l = alpha_scale * sqrt(eps_l) / p  (Theorem 4.1 form), p = N / d* */
+  int eps_frozen;       /* nonzero: keep iteration 0's eps for the whole run */
+  double tol;           /* tolerance of the stop rule */
+  int max_iter;
+  int stop_rule;        /* TTC_STOP_* */
+  int check_every;      /* evaluate the stop rule every k iterations (>= 1) */
+  double polish_below;  /* MIXED: switch to FP64 once the relative residual is below this */
+  int use_graph;        /* nonzero: replay one CUDA graph per iteration */
+} ttc_options;
+
+typedef struct {
+  double eps;           /* eps_l used */
+  double alpha;         /* alpha_l used */
+  double res_norm;      /* ||P_Omega(T_l - T*)||_F before the step */
+  int precision_used;   /* TTC_PREC_FP64 or TTC_PREC_FP32 for the Omega pass of this step */
+} ttc_step_info;
+
+typedef struct {
+  int iters;
+  int converged;        /* 1 if the stop rule was met */
+  double last_metric;   /* last value of the stop-rule metric */
+  double res_norm;      /* residual norm at the last step */
+  int polish_iter;      /* first FP64 iteration in MIXED mode (-1: none) */
+} ttc_solve_info;
+
+/* Fill `opt` with defaults: MIXED precision, eps_rel 1, alpha_scale 1.5,
+ * tol 1e-6, max_iter 500, stop rule RELERR, check_every 1, polish_below 1e-5,
+ * graphs on. */
+void ttc_default_options(ttc_options* opt);
+
+/* Create a context for order d (1 < d <= 16), mode sizes n[d] (n_k >= 1),
+ * TT-ranks r[d+1] with r[0] = r[d] = 1 and 1 <= r[k] <= 32.  `opt` may be
+ * NULL (defaults).  `cuda_stream` (a cudaStream_t, may be NULL) is the stream
+ * all work of this context is issued on; NULL makes the context create its
+ * own.  On success *out owns the context; free it with ttc_destroy. */
+int ttc_create(ttc_ctx** out, int d, const int64_t* n, const int32_t* r,
+               const ttc_options* opt, void* cuda_stream);
+
+/* Copy the observations in: N >= 1 index rows idx[N*d] (int32, 0-based) and
+ * values y[N] (FP64).  The device validates every coordinate (TTC_ERANGE),
+ * rejects repeated indices (TTC_EDUP) and non-finite values
+ * (TTC_ENONFINITE), then builds the per-mode layout: packed coordinates and,
+ * for each mode k, a stable sort of the entries by x_k into segments
+ * (Omega ordered by slice of mode k, ties in input order).  Replaces any
+ * previous observations. */
+int ttc_set_observations(ttc_ctx* ctx, int64_t N, const int32_t* idx, const double* y);
+
+/* Set the current iterate T_l from host cores (see the layout above). */
+int ttc_set_cores(ttc_ctx* ctx, const double* const* cores);
+
+/* Copy the current iterate out to caller-allocated host cores. */
+int ttc_get_cores(ttc_ctx* ctx, double* const* cores_out);
+
+/* Ground truth T* as TT cores of ranks rt[d+1] (rt[0] = rt[d] = 1, each
+ * <= 32); enables TTC_STOP_RELERR and ttc_relerr. */
+int ttc_set_truth(ttc_ctx* ctx, const int32_t* rt, const double* const* cores);
+
+/* One PRGD iteration (Algorithm 2).  alpha <= 0 takes the step-size policy
+ * of the options.  With `out` non-NULL the call waits for the iteration and
+ * fills `out` (TTC_ENONFINITE if the residual is not finite); with `out` NULL
+ * it only enqueues the iteration on the context's stream and returns. */
+int ttc_step(ttc_ctx* ctx, double alpha, ttc_step_info* out);
+
+/* Iterate until the options' stop rule holds or max_iter.  Returns TTC_OK
+ * when converged (or the rule is NONE), TTC_ENOTCONV otherwise. */
+int ttc_solve(ttc_ctx* ctx, ttc_solve_info* out);
+
+/* ||T_l - T*||_F / ||T*||_F for the current iterate (needs ttc_set_truth). */
+int ttc_relerr(ttc_ctx* ctx, double* out);
+
+/* Evaluate the current iterate at M index rows (host in, host out), in the
+ * given precision (TTC_PREC_FP64 or TTC_PREC_FP32); Eq. (TT Core). */
+int ttc_eval(ttc_ctx* ctx, int64_t M, const int32_t* idx, int precision, double* out);
+
+/* Intermediate results, for checking:
+ *   ttc_get_residual: g[N] = T(omega) - y(omega) in input order at the
+ *     CURRENT iterate (runs one extra sampled pass, which also overwrites the
+ *     slice energies and scatter below);
+ * and, for the iterate the last ttc_step started from:
+ *   ttc_get_slice_energy: s_k[n_k], the mode-k slice energies of G_l
+ *     (diag(M_k(G_l) M_k(G_l)^T), Section 3.2);
+ *   ttc_get_scatter: E_k, n_k x r_{k-1} x r_k, the sum over the mode-k slice
+ *     x of g * (T^{<=k-1})^T (T^{>=k+1})^T at the iterate's own cores (the
+ *     sparse factor of Eq. (tsp in nm) before the weight and gauge factors).
+ */
+int ttc_get_residual(ttc_ctx* ctx, double* g_out);
+int ttc_get_slice_energy(ttc_ctx* ctx, int k, double* s_out);
+int ttc_get_scatter(ttc_ctx* ctx, int k, double* E_out);
+
+/* Layout of mode k, for checking: perm[N] (input position of the j-th entry
+ * in mode-k order) and seg_off[n_k + 1] (CSR offsets of the slices). */
+int ttc_get_layout(ttc_ctx* ctx, int k, int32_t* perm_out, int64_t* seg_off_out);
+
+/* Kernel timing: when enabled, the dominant kernel of every iteration (the
+ * sampled pass over Omega) is bracketed by CUDA events on the context's
+ * stream, also inside the replayed CUDA graph (event-record nodes).  Every
+ * iteration then waits for that kernel's end event on the host and adds its
+ * duration; *ms and *count return the accumulated duration and number of
+ * timed launches since the last reset. */
+int ttc_profile_enable(ttc_ctx* ctx, int on);
+int ttc_profile_read(ttc_ctx* ctx, double* ms, int64_t* count, int reset);
+
+/* Number of kernels this context has launched so far (a graph replay counts
+ * every kernel node it runs). */
+int ttc_launch_count(ttc_ctx* ctx, int64_t* launches);
+
+/* Device bytes held by the context. */
+int ttc_device_bytes(ttc_ctx* ctx, int64_t* bytes);
+
+void ttc_destroy(ttc_ctx* ctx);
+
+const char* ttc_strerror(int status);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char* ttc_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTC_H */

@@ -1,0 +1,141 @@
+// Shared definitions of the ttc CUDA library: limits, the device-side problem
+// descriptor, error plumbing and block-level small dense linear algebra used
+// by the FP64 stages (Grams, SPD inverses, symmetric eigendecomposition).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ttc.h"
+
+#define TTC_MAXM 16      // maximum tensor order
+#define TTC_MAXR 32      // maximum TT-rank
+#define TTC_MAXQ 64      // maximum rank of the rank-2r TT of the retraction
+#define TTC_CHUNK 128    // Omega entries per block of the sampled pass
+#define TTC_NT 128       // threads per block of the sampled pass
+
+// ---------------------------------------------------------------------------
+// Device descriptor of one completion problem.  Everything the kernels touch
+// is reachable from here; the host fills it once per layout.
+// Core k (0-based) is stored slice-major: T_k(x) is an r[k] x r[k+1]
+// row-major block at offset x * r[k] * r[k+1].
+// ---------------------------------------------------------------------------
+struct DevProb {
+  int m;
+  int N;
+  int W;                       // 32-bit code words per entry (1, 2 or 4)
+  int n[TTC_MAXM];
+  int r[TTC_MAXM + 1];
+  int cword[TTC_MAXM];         // code word holding mode k
+  int cshift[TTC_MAXM];        // bit offset of mode k in that word
+  int cbits[TTC_MAXM];         // bits of mode k
+  double p;                    // N / d*
+  double inv_min_n;            // 1 / min_k n_k
+  int keep_residual;           // write g[] in input order during the pass
+
+  // current iterate
+  double* core64[TTC_MAXM];
+  float* core32[TTC_MAXM];
+  double* prev64[TTC_MAXM];    // copy of T_l for the step-change metric
+
+  // Omega layout, per mode, in mode-k order
+  const uint32_t* code[TTC_MAXM];
+  const float* y32[TTC_MAXM];
+  const double* y64[TTC_MAXM];
+  const int* perm[TTC_MAXM];
+  const int* seg[TTC_MAXM];      // n_k + 1 offsets
+  const int* cfirst[TTC_MAXM];   // n_k + 1: chunks of slice x are [cfirst[x], cfirst[x+1])
+  const int* cseg[TTC_MAXM];     // slice of each chunk
+  int nchunk[TTC_MAXM];
+  int chunk_base[TTC_MAXM + 1];  // prefix of nchunk over modes
+  void* part;                    // chunk partials: [chunk][1 + r_k r_{k+1}] (float or double)
+  int part_stride;               // elements per chunk partial (max over modes)
+
+  // outputs of the Omega pass
+  double* s[TTC_MAXM];           // slice energies, n_k
+  double* E[TTC_MAXM];           // n_k x r_k x r_{k+1}
+  double* g;                     // residual in input order (when keep_residual)
+
+  // dense-stage buffers
+  double* C[TTC_MAXM];           // rank-2r cores, n_k x q_k x q_{k+1}
+  int q[TTC_MAXM + 1];
+  double* small;                 // small matrices, offsets below
+  int off_lam[TTC_MAXM + 1];     // Lam[k]: r_k x r_k, left Gram of W^{1/2} T up to core k-1
+  int off_gam[TTC_MAXM + 1];     // Gam[k]: r_k x r_k, right Gram of W^{1/2} T from core k
+  int off_lami[TTC_MAXM + 1];    // inverse of Lam[k]
+  int off_gami[TTC_MAXM + 1];    // inverse of Gam[k]
+  int off_h[TTC_MAXM];           // H_k = sum_x T_k(x)^T E_k(x): r_{k+1} x r_{k+1}
+  int off_qm[TTC_MAXM];          // Q_k = Lam[k+1]^{-1} H_k Gam[k+1]^{-1}
+  int off_psi[TTC_MAXM + 1];     // Psi[k]: q_k x q_k right Gram of the rank-2r TT
+  int off_nk[TTC_MAXM];          // N_k: q_{k+1} x q_{k+1}
+  int off_pk[TTC_MAXM];          // P_k: q_{k+1} x r_{k+1}
+  int off_sk[TTC_MAXM];          // S_k: r_{k+1} x q_{k+1}
+  double* red;                   // partial sums of slice reductions
+  int red_stride;                // doubles per reduction block
+  double* scal;                  // scalars, see SC_* below
+
+  // ground truth (optional)
+  int has_truth;
+  int rt[TTC_MAXM + 1];
+  double* truth[TTC_MAXM];
+  long long dstar;               // product of n_k (0 if it overflows)
+};
+
+enum {
+  SC_G2 = 0,        // ||g||^2
+  SC_EPS = 1,
+  SC_ALPHA = 2,
+  SC_ALPHA_OVR = 3, // > 0: use this step size
+  SC_EPS_FIXED = 4, // > 0: use this eps
+  SC_FLAGS = 5,     // bit 0: non-finite seen; bit 1: lost rank in the retraction
+  SC_METRIC = 6,    // last metric (sum of squares)
+  SC_NORM = 7,      // reference norm^2 of the metric
+  SC_EPS_REL = 8,
+  SC_ALPHA_SCALE = 9,
+  SC_COUNT = 16
+};
+
+// ---------------------------------------------------------------------------
+// error plumbing (host)
+// ---------------------------------------------------------------------------
+void ttc_record_cuda_error(cudaError_t e);
+#define TTC_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) {                             \
+      ttc_record_cuda_error(_e);                         \
+      return TTC_ECUDA;                                  \
+    }                                                    \
+  } while (0)
+#define TTC_TRY(call)                                    \
+  do {                                                   \
+    int _s = (call);                                     \
+    if (_s != TTC_OK) return _s;                         \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int code_coord(const DevProb& P, const uint32_t* words, int k) {
+  return (int)((words[P.cword[k]] >> P.cshift[k]) & ((1u << P.cbits[k]) - 1u));
+}
+
+// C (M x N, ldc) = alpha * op(A) * op(B) (+ beta * C when accumulate), on data
+// visible to the whole block; threads stride over the M*N outputs.  The caller
+// synchronises.  op(A) is M x K: A[i*lda + k] or, transposed, A[k*lda + i].
+template <typename T>
+__device__ void blk_gemm(int M, int N, int K, const T* A, int lda, bool ta, const T* B, int ldb,
+                         bool tb, T* C, int ldc, T alpha, bool accumulate) {
+  for (int idx = threadIdx.x; idx < M * N; idx += blockDim.x) {
+    int i = idx / N, j = idx - (idx / N) * N;
+    T acc = 0;
+    for (int k = 0; k < K; ++k) {
+      T a = ta ? A[k * lda + i] : A[i * lda + k];
+      T b = tb ? B[j * ldb + k] : B[k * ldb + j];
+      acc = fma(a, b, acc);
+    }
+    C[i * ldc + j] = accumulate ? fma(alpha, acc, C[i * ldc + j]) : alpha * acc;
+  }
+}
+
+// Block-level small dense linear algebra lives in linalg.cuh.

@@ -1,0 +1,73 @@
+// Host-side context of one completion problem and the internal entry points
+// the C ABI (api.cu) calls into.  Device memory is owned through DevBuf and
+// released by ttc_destroy.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct ttc_ctx {
+  int m = 0;
+  long long n[TTC_MAXM] = {0};
+  int r[TTC_MAXM + 1] = {0};
+  ttc_options opt;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int N = 0;
+  bool have_obs = false;
+  bool have_cores = false;
+  int rank_bucket = 4;             // compile-time rank bound used by the Omega-pass kernels
+
+  DevProb hp;                       // host mirror of the descriptor
+  DevProb* dp = nullptr;            // device copy
+  std::vector<DevBuf> bufs;         // every device allocation (freed on destroy)
+  std::vector<DevBuf> obs_bufs;     // allocations that depend on the observations
+  size_t device_bytes = 0;
+
+  // graphs of one iteration: [0] Omega pass in FP32, [1] in FP64
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graph_dirty = true;
+
+  // profiling of the Omega pass
+  bool prof = false;
+  cudaEvent_t ev_beg = nullptr, ev_end = nullptr;
+  double prof_ms = 0.0;
+  long long prof_count = 0;
+
+  // kernel launches: enqueued so far (graph replays add their kernel nodes)
+  long long nlaunch = 0;
+  long long graph_kernels[2] = {0, 0};
+
+  // solver state
+  int iter = 0;
+  bool eps_set = false;
+  int cur_prec = TTC_PREC_FP64;    // precision of the Omega pass for the next step
+  double alpha_ovr = 0.0;           // step-size override currently on the device
+};
+
+// allocation helpers (api.cu)
+int ttc_alloc(ttc_ctx* c, void** p, size_t bytes, bool obs);
+void ttc_free_obs(ttc_ctx* c);
+int ttc_upload_desc(ttc_ctx* c);
+
+// layout.cu
+int ttc_build_layout(ttc_ctx* c, const int32_t* idx_host, const double* y_host);
+
+// omega_pass.cu
+int ttc_prepare_omega_pass();
+int ttc_launch_omega_pass(ttc_ctx* c, int prec);
+int ttc_launch_eval(ttc_ctx* c, const int32_t* idx_dev, long long M, int prec, double* out_dev);
+
+// dense.cu
+int ttc_alloc_dense(ttc_ctx* c);
+int ttc_launch_dense(ttc_ctx* c);
+int ttc_launch_metric(ttc_ctx* c, int which);   // 0: ||T - T*||^2 , 1: ||T_l - T_{l-1}||^2
+int ttc_launch_save_prev(ttc_ctx* c);
+int ttc_launch_mirror32(ttc_ctx* c);
+void ttc_free_plan(const ttc_ctx* c);

@@ -1,0 +1,277 @@
+"""Thin Python binding of the ttc C ABI (include/ttc.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library libttc.so.  Importing this module never falls back to a CPU path: if
+the library is missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libttc.so")
+
+PREC_FP64, PREC_MIXED, PREC_FP32 = 0, 1, 2
+STOP_RELERR, STOP_STEP, STOP_NONE = 0, 1, 2
+
+STATUS = {
+    0: "TTC_OK", -1: "TTC_EINVAL", -2: "TTC_ENOMEM", -3: "TTC_ERANGE", -4: "TTC_EDUP",
+    -5: "TTC_ENONFINITE", -6: "TTC_ENOTCONV", -7: "TTC_ETIMEOUT", -8: "TTC_ECUDA", -9: "TTC_EBUSY",
+    -10: "TTC_EUNSUPPORTED",
+}
+
+
+class TTCError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {STATUS.get(status, status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int), ("eps_rel", C.c_double), ("alpha_scale", C.c_double),
+        ("eps_frozen", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("stop_rule", C.c_int),
+        ("check_every", C.c_int), ("polish_below", C.c_double), ("use_graph", C.c_int),
+    ]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("eps", C.c_double), ("alpha", C.c_double), ("res_norm", C.c_double), ("precision_used", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("last_metric", C.c_double),
+                ("res_norm", C.c_double), ("polish_iter", C.c_int)]
+
+
+_lib = None
+
+EXPORTS = [
+    "ttc_default_options", "ttc_create", "ttc_set_observations", "ttc_set_cores", "ttc_get_cores",
+    "ttc_set_truth", "ttc_step", "ttc_solve", "ttc_relerr", "ttc_eval", "ttc_get_residual",
+    "ttc_get_slice_energy", "ttc_get_scatter", "ttc_get_layout", "ttc_profile_enable", "ttc_profile_read",
+    "ttc_device_bytes", "ttc_destroy", "ttc_strerror", "ttc_last_cuda_error", "ttc_launch_count",
+]
+
+
+def lib():
+    """Load libttc.so (built by paper_2501_13385_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built: call __graft_entry__.build() or "
+                           "paper_2501_13385_gb300.build.build() first")
+    L = C.CDLL(LIB_PATH)
+    vp, i32p, i64p, dp = C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_double)
+    dpp = C.POINTER(dp)
+    sig = {
+        "ttc_default_options": (None, [C.POINTER(Options)]),
+        "ttc_create": (C.c_int, [C.POINTER(vp), C.c_int, i64p, i32p, C.POINTER(Options), vp]),
+        "ttc_set_observations": (C.c_int, [vp, C.c_int64, i32p, dp]),
+        "ttc_set_cores": (C.c_int, [vp, dpp]),
+        "ttc_get_cores": (C.c_int, [vp, dpp]),
+        "ttc_set_truth": (C.c_int, [vp, i32p, dpp]),
+        "ttc_step": (C.c_int, [vp, C.c_double, C.POINTER(StepInfo)]),
+        "ttc_solve": (C.c_int, [vp, C.POINTER(SolveInfo)]),
+        "ttc_relerr": (C.c_int, [vp, dp]),
+        "ttc_eval": (C.c_int, [vp, C.c_int64, i32p, C.c_int, dp]),
+        "ttc_get_residual": (C.c_int, [vp, dp]),
+        "ttc_get_slice_energy": (C.c_int, [vp, C.c_int, dp]),
+        "ttc_get_scatter": (C.c_int, [vp, C.c_int, dp]),
+        "ttc_get_layout": (C.c_int, [vp, C.c_int, i32p, i64p]),
+        "ttc_profile_enable": (C.c_int, [vp, C.c_int]),
+        "ttc_profile_read": (C.c_int, [vp, dp, i64p, C.c_int]),
+        "ttc_device_bytes": (C.c_int, [vp, i64p]),
+        "ttc_launch_count": (C.c_int, [vp, i64p]),
+        "ttc_destroy": (None, [vp]),
+        "ttc_strerror": (C.c_char_p, [C.c_int]),
+        "ttc_last_cuda_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        detail = ""
+        if status == -8:
+            detail = lib().ttc_last_cuda_error().decode()
+        raise TTCError(status, where, detail)
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().ttc_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """One completion problem on the GPU (ttc_ctx)."""
+
+    def __init__(self, n: Sequence[int], r: Sequence[int], options: Optional[Options] = None,
+                 stream: Optional[int] = None, **kw):
+        L = lib()
+        self.n = [int(x) for x in n]
+        self.r = [int(x) for x in r]
+        self.m = len(self.n)
+        opt = options if options is not None else default_options(**kw)
+        self._h = C.c_void_p()
+        na = np.asarray(self.n, dtype=np.int64)
+        ra = np.asarray(self.r, dtype=np.int32)
+        _check(L.ttc_create(C.byref(self._h), self.m, na.ctypes.data_as(C.POINTER(C.c_int64)),
+                            ra.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(opt),
+                            C.c_void_p(stream) if stream else None), "ttc_create")
+        self.N = 0
+
+    # -- lifetime
+    def close(self):
+        if self._h:
+            lib().ttc_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- data in / out
+    def set_observations(self, idx, y):
+        idx, ip = _i32(idx)
+        y, yp = _f64(y)
+        if idx.ndim != 2 or idx.shape[1] != self.m or y.shape[0] != idx.shape[0]:
+            raise ValueError("idx must be (N, d) and y (N,)")
+        _check(lib().ttc_set_observations(self._h, idx.shape[0], ip, yp), "ttc_set_observations")
+        self.N = idx.shape[0]
+
+    def _core_ptrs(self, cores, ranks):
+        arrs = []
+        for k in range(self.m):
+            c = np.ascontiguousarray(cores[k], dtype=np.float64)
+            if c.shape != (ranks[k], self.n[k], ranks[k + 1]):
+                raise ValueError(f"core {k} has shape {c.shape}, expected {(ranks[k], self.n[k], ranks[k + 1])}")
+            arrs.append(c)
+        ptrs = (C.POINTER(C.c_double) * self.m)(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs])
+        return arrs, ptrs
+
+    def set_cores(self, cores):
+        arrs, ptrs = self._core_ptrs(cores, self.r)
+        _check(lib().ttc_set_cores(self._h, ptrs), "ttc_set_cores")
+
+    def get_cores(self) -> List[np.ndarray]:
+        arrs = [np.empty((self.r[k], self.n[k], self.r[k + 1])) for k in range(self.m)]
+        ptrs = (C.POINTER(C.c_double) * self.m)(*[a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs])
+        _check(lib().ttc_get_cores(self._h, ptrs), "ttc_get_cores")
+        return arrs
+
+    def set_truth(self, cores):
+        rt = [1] + [int(c.shape[2]) for c in cores[:-1]] + [1]
+        arrs, ptrs = self._core_ptrs(cores, rt)
+        ra = np.asarray(rt, dtype=np.int32)
+        _check(lib().ttc_set_truth(self._h, ra.ctypes.data_as(C.POINTER(C.c_int32)), ptrs), "ttc_set_truth")
+
+    # -- iteration
+    def step_async(self, alpha: float = 0.0):
+        """Enqueue one iteration on the context's stream without waiting."""
+        _check(lib().ttc_step(self._h, float(alpha), None), "ttc_step")
+
+    def step(self, alpha: float = 0.0) -> dict:
+        info = StepInfo()
+        _check(lib().ttc_step(self._h, float(alpha), C.byref(info)), "ttc_step")
+        return {"eps": info.eps, "alpha": info.alpha, "res_norm": info.res_norm,
+                "precision_used": info.precision_used}
+
+    def solve(self, raise_on_notconv: bool = False) -> dict:
+        info = SolveInfo()
+        st = lib().ttc_solve(self._h, C.byref(info))
+        if st not in (0, -6) or (raise_on_notconv and st == -6):
+            _check(st, "ttc_solve")
+        return {"status": STATUS.get(st, st), "iters": info.iters, "converged": bool(info.converged),
+                "last_metric": info.last_metric, "res_norm": info.res_norm, "polish_iter": info.polish_iter}
+
+    def relerr(self) -> float:
+        v = C.c_double()
+        _check(lib().ttc_relerr(self._h, C.byref(v)), "ttc_relerr")
+        return v.value
+
+    def eval(self, idx, precision: int = PREC_FP64) -> np.ndarray:
+        idx, ip = _i32(idx)
+        out = np.empty(idx.shape[0])
+        _check(lib().ttc_eval(self._h, idx.shape[0], ip, precision, out.ctypes.data_as(C.POINTER(C.c_double))),
+               "ttc_eval")
+        return out
+
+    # -- intermediate results of the last step
+    def residual(self) -> np.ndarray:
+        out = np.empty(self.N)
+        _check(lib().ttc_get_residual(self._h, out.ctypes.data_as(C.POINTER(C.c_double))), "ttc_get_residual")
+        return out
+
+    def slice_energy(self, k: int) -> np.ndarray:
+        out = np.empty(self.n[k])
+        _check(lib().ttc_get_slice_energy(self._h, k, out.ctypes.data_as(C.POINTER(C.c_double))),
+               "ttc_get_slice_energy")
+        return out
+
+    def scatter(self, k: int) -> np.ndarray:
+        """E_k as (n_k, r_{k-1}, r_k)."""
+        out = np.empty((self.n[k], self.r[k], self.r[k + 1]))
+        _check(lib().ttc_get_scatter(self._h, k, out.ctypes.data_as(C.POINTER(C.c_double))), "ttc_get_scatter")
+        return out
+
+    def layout(self, k: int):
+        perm = np.empty(self.N, dtype=np.int32)
+        seg = np.empty(self.n[k] + 1, dtype=np.int64)
+        _check(lib().ttc_get_layout(self._h, k, perm.ctypes.data_as(C.POINTER(C.c_int32)),
+                                    seg.ctypes.data_as(C.POINTER(C.c_int64))), "ttc_get_layout")
+        return perm, seg
+
+    # -- profiling
+    def profile_enable(self, on: bool = True):
+        _check(lib().ttc_profile_enable(self._h, 1 if on else 0), "ttc_profile_enable")
+
+    def profile_read(self, reset: bool = False):
+        ms = C.c_double()
+        cnt = C.c_int64()
+        _check(lib().ttc_profile_read(self._h, C.byref(ms), C.byref(cnt), 1 if reset else 0), "ttc_profile_read")
+        return ms.value, cnt.value
+
+    def launch_count(self) -> int:
+        v = C.c_int64()
+        _check(lib().ttc_launch_count(self._h, C.byref(v)), "ttc_launch_count")
+        return v.value
+
+    def device_bytes(self) -> int:
+        v = C.c_int64()
+        _check(lib().ttc_device_bytes(self._h, C.byref(v)), "ttc_device_bytes")
+        return v.value

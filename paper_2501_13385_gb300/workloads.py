@@ -373,3 +373,16 @@ CONFIGS = {
     "hyperspectral_like": hyperspectral_like,
     "tomography_like": tomography_like,
 }
+
+
+def random_problem(seed: int, n: Sequence[int], r: Sequence[int], count: int, noise_std: float = 0.0,
+                   init_rel: float = 0.1) -> Problem:
+    """Small generic instance for edge cases: Gaussian truth cores of ranks r
+    scaled to unit-size entries, `count` uniform entries without replacement,
+    optional additive noise, start = truth perturbed by `init_rel`."""
+    n, r = list(n), list(r)
+    rng = Rng(seed, 6)
+    cores = _gaussian_cores(rng, n, r)
+    for k in range(len(n)):
+        cores[k] /= math.sqrt(r[k])
+    return _finish(f"random{seed}", n, r, cores, rng, count, noise_std, "abs", init_rel, seed)

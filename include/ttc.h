@@ -176,6 +176,34 @@ int ttc_launch_count(ttc_ctx* ctx, int64_t* launches);
 /* Device bytes held by the context. */
 int ttc_device_bytes(ttc_ctx* ctx, int64_t* bytes);
 
+/* Allocation-free squared Frobenius distance of two tensor trains (the paper
+ * has no counterpart of this call).  For callers that may not allocate
+ * device memory themselves, e.g. a real-time loop with a fixed memory budget
+ * or code inside a framework that owns every device allocation: the caller
+ * passes the inputs and the output in its own device memory, and the call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * Inputs: order d (1 <= d <= 16), mode sizes n[d] (host), TT-ranks ra[d+1]
+ * and rb[d+1] (host, first and last 1, each <= 32), and host arrays of d
+ * DEVICE pointers a_dev[k], b_dev[k] to cores in the host layout of this
+ * header (ra[k] x n[k] x ra[k+1] row-major).  Every one of the d* = prod n_k
+ * entries is evaluated in FP64, so d* is limited to 2^32; larger shapes return
+ * TTC_EUNSUPPORTED.  Output: out_dev[0] = ||A - B||_F^2, out_dev[1] =
+ * ||B||_F^2 (two doubles of device memory), written on `cuda_stream` (NULL:
+ * the default stream); the call returns without waiting.
+ *
+ * Scratch: per-block partial sums live in one fixed 16 KiB device array
+ * (1024 partial pairs) that every GPU loading the library holds until the
+ * process exits; it is never cleared (each call writes the slots it reads).
+ * All calls share it, so calls that overlap on the GPU (different streams or
+ * host threads without ordering) race.  The first call on each device looks
+ * up the array's device address with that device current; make that first
+ * call before any stream capture.  Errors: TTC_EINVAL (null pointers, bad
+ * ranks), TTC_EUNSUPPORTED (limits above), TTC_ECUDA (launch failure). */
+int ttc_tt_dist2_static(int d, const int64_t* n, const int32_t* ra, const double* const* a_dev,
+                        const int32_t* rb, const double* const* b_dev, double* out_dev,
+                        void* cuda_stream);
+
 void ttc_destroy(ttc_ctx* ctx);
 
 const char* ttc_strerror(int status);

@@ -58,6 +58,7 @@ EXPORTS = [
     "ttc_set_truth", "ttc_step", "ttc_solve", "ttc_relerr", "ttc_eval", "ttc_get_residual",
     "ttc_get_slice_energy", "ttc_get_scatter", "ttc_get_layout", "ttc_profile_enable", "ttc_profile_read",
     "ttc_device_bytes", "ttc_destroy", "ttc_strerror", "ttc_last_cuda_error", "ttc_launch_count",
+    "ttc_tt_dist2_static",
 ]
 
 
@@ -91,6 +92,7 @@ def lib():
         "ttc_profile_read": (C.c_int, [vp, dp, i64p, C.c_int]),
         "ttc_device_bytes": (C.c_int, [vp, i64p]),
         "ttc_launch_count": (C.c_int, [vp, i64p]),
+        "ttc_tt_dist2_static": (C.c_int, [C.c_int, i64p, i32p, C.POINTER(vp), i32p, C.POINTER(vp), vp, vp]),
         "ttc_destroy": (None, [vp]),
         "ttc_strerror": (C.c_char_p, [C.c_int]),
         "ttc_last_cuda_error": (C.c_char_p, []),

@@ -82,6 +82,7 @@ typedef struct {
   double alpha;         /* alpha_l used */
   double res_norm;      /* ||P_Omega(T_l - T*)||_F before the step */
   int precision_used;   /* TTC_PREC_FP64 or TTC_PREC_FP32 for the Omega pass of this step */
+  int subspace_iters;   /* iterations the retraction's subspace solves took (all bonds) */
 } ttc_step_info;
 
 typedef struct {

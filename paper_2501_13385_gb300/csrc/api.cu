@@ -217,6 +217,7 @@ int ttc_create(ttc_ctx** out, int d, const int64_t* n, const int32_t* r, const t
     if (n[k] < minn) minn = n[k];
   }
   for (int k = 0; k <= d; ++k) P.r[k] = r[k];
+  P.R = c->rank_bucket;
   P.dstar = ovf ? 0 : dl;
   P.inv_min_n = 1.0 / (double)minn;
   (void)dstar;
@@ -235,7 +236,11 @@ int ttc_create(ttc_ctx** out, int d, const int64_t* n, const int32_t* r, const t
   for (int k = 0; k < d && s == TTC_OK; ++k) {
     size_t cnt = (size_t)n[k] * r[k] * r[k + 1];
     if ((s = ttc_alloc(c, (void**)&P.core64[k], sizeof(double) * cnt, false)) != TTC_OK) break;
-    if ((s = ttc_alloc(c, (void**)&P.core32[k], sizeof(float) * cnt, false)) != TTC_OK) break;
+    size_t padcnt = (size_t)n[k] * c->rank_bucket * c->rank_bucket;
+    if ((s = ttc_alloc(c, (void**)&P.core32p[k], sizeof(float) * padcnt, false)) != TTC_OK) break;
+    if ((s = ttc_alloc(c, (void**)&P.core64p[k], sizeof(double) * padcnt, false)) != TTC_OK) break;
+    cudaMemset(P.core32p[k], 0, sizeof(float) * padcnt);
+    cudaMemset(P.core64p[k], 0, sizeof(double) * padcnt);
     if ((s = ttc_alloc(c, (void**)&P.s[k], sizeof(double) * (size_t)n[k], false)) != TTC_OK) break;
     if ((s = ttc_alloc(c, (void**)&P.E[k], sizeof(double) * cnt, false)) != TTC_OK) break;
   }
@@ -366,12 +371,14 @@ static int step_impl(ttc_ctx* c, double alpha, ttc_step_info* out, bool sync_inf
   if (sync_info || out) {
     double sc[SC_COUNT];
     TTC_TRY(read_scalars(c, sc));
-    int flags = (int)sc[SC_FLAGS];
+    unsigned flags;
+    memcpy(&flags, &sc[SC_FLAGS], sizeof(flags));
     if (out) {
       out->eps = sc[SC_EPS];
       out->alpha = sc[SC_ALPHA];
       out->res_norm = std::sqrt(sc[SC_G2]);
       out->precision_used = prec;
+      out->subspace_iters = (int)sc[SC_SUBIT];
     }
     if (flags & 1) return TTC_ENONFINITE;
   }
@@ -424,7 +431,9 @@ int ttc_solve(ttc_ctx* c, ttc_solve_info* out) {
     }
     double sc[SC_COUNT];
     TTC_TRY(read_scalars(c, sc));
-    if (((int)sc[SC_FLAGS]) & 1) {
+    unsigned flags;
+    memcpy(&flags, &sc[SC_FLAGS], sizeof(flags));
+    if (flags & 1u) {
       status = TTC_ENONFINITE;
       break;
     }

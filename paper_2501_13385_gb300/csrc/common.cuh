@@ -11,8 +11,8 @@
 #define TTC_MAXM 16      // maximum tensor order
 #define TTC_MAXR 32      // maximum TT-rank
 #define TTC_MAXQ 64      // maximum rank of the rank-2r TT of the retraction
-#define TTC_CHUNK 128    // Omega entries per block of the sampled pass
-#define TTC_NT 128       // threads per block of the sampled pass
+#define TTC_CHUNK 1024   // Omega entries per block of the sampled pass
+#define TTC_NT 256       // threads per block of the sampled pass
 
 // ---------------------------------------------------------------------------
 // Device descriptor of one completion problem.  Everything the kernels touch
@@ -34,8 +34,13 @@ struct DevProb {
   int keep_residual;           // write g[] in input order during the pass
 
   // current iterate
-  double* core64[TTC_MAXM];
-  float* core32[TTC_MAXM];
+  double* core64[TTC_MAXM];    // FP64 master, slice-major, unpadded
+  // padded mirrors read by the sampled pass: slice x of core k starts at
+  // x * R * R (16-byte aligned); row a of the slice starts at a * R, except for
+  // cores with r_{k+1} = 1 whose slice is one contiguous vector
+  int R;                       // rank bucket (4, 8, 16 or 32) = row stride
+  float* core32p[TTC_MAXM];
+  double* core64p[TTC_MAXM];
   double* prev64[TTC_MAXM];    // copy of T_l for the step-change metric
 
   // Omega layout, per mode, in mode-k order
@@ -70,9 +75,12 @@ struct DevProb {
   int off_nk[TTC_MAXM];          // N_k: q_{k+1} x q_{k+1}
   int off_pk[TTC_MAXM];          // P_k: q_{k+1} x r_{k+1}
   int off_sk[TTC_MAXM];          // S_k: r_{k+1} x q_{k+1}
+  int off_mlam[3][TTC_MAXM + 1];  // metric Gram sweep: A^T A, A^T B, B^T B left Grams
   double* red;                   // partial sums of slice reductions
-  int red_stride;                // doubles per reduction block
+  long long red_metric;          // offset of the metric's partials in red
   double* scal;                  // scalars, see SC_* below
+  unsigned* flags;               // = (unsigned*)(scal + SC_FLAGS): bit 0 non-finite, bit 1 lost rank
+  int* counters;                 // completion counters of the fused reductions (reset by their last block)
 
   // ground truth (optional)
   int has_truth;
@@ -92,6 +100,7 @@ enum {
   SC_NORM = 7,      // reference norm^2 of the metric
   SC_EPS_REL = 8,
   SC_ALPHA_SCALE = 9,
+  SC_SUBIT = 10,    // subspace iterations of the retraction in the last iteration (all bonds)
   SC_COUNT = 16
 };
 
@@ -116,6 +125,11 @@ void ttc_record_cuda_error(cudaError_t e);
 // ---------------------------------------------------------------------------
 // device helpers
 // ---------------------------------------------------------------------------
+// offset of element (a, b) inside a padded slice of core k
+__device__ __forceinline__ int pad_idx(const DevProb& P, int k, int a, int b) {
+  return P.r[k + 1] == 1 ? a : a * P.R + b;
+}
+
 __device__ __forceinline__ int code_coord(const DevProb& P, const uint32_t* words, int k) {
   return (int)((words[P.cword[k]] >> P.cshift[k]) & ((1u << P.cbits[k]) - 1u));
 }

@@ -1,36 +1,48 @@
-// Dense stage of one PRGD iteration, all in FP64 on the device:
+// Dense stage of one PRGD iteration on the device (FP64 results):
 //
-//  (1) eps_l, alpha_l from ||G_l||^2 (step-size form of Theorem 4.1);
+//  (1) eps_l, alpha_l from ||G_l||^2 (step-size form of Theorem 4.1); done by
+//      the last block of the slice reduction of the sampled pass.
 //      G_k(x) = eps + s_k(x) is the diagonal of G_{l,k} (Section 3.2).
 //  (2) Grams of T^ = W^{1/2} T (Proposition 3.1: T^_k(x) = G_k(x)^{1/(4m)} T_k(x)):
 //        Lam[k+1] = sum_x G_k(x)^{1/(2m)} T_k(x)^T Lam[k] T_k(x)      (left)
 //        Gam[k]   = sum_x G_k(x)^{1/(2m)} T_k(x) Gam[k+1] T_k(x)^T    (right)
 //      and H_k = sum_x T_k(x)^T E_k(x).
-//  (3) The weighted tangent projection of Lemma 3.5 (Eq. (tsp in nm)),
-//      taken at the left-orthogonal decomposition U of T^ with T^<=k = U^<=k R_k,
+//  (3) The weighted tangent projection of Lemma 3.5 (Eq. (tsp in nm)), taken
+//      at the left-orthogonal decomposition U of T^ with T^<=k = U^<=k R_k,
 //      R_k^T R_k = Lam[k], written back in the gauge of the iterate's own
-//      cores.  With the sparse factor E_k from the sampled pass, the update
-//      core of W_l = T_l - alpha tilde P_T W^{-1} G_l for mode k becomes
+//      cores.  With the sparse factor E_k of the sampled pass, the update core
+//      of W_l = T_l - alpha tilde P_T W^{-1} G_l for mode k is
 //        B_k(x) = -alpha [ G_k(x)^{-1/(2m)} Lam[k]^{-1} E_k(x) Gam[k+1]^{-1}
 //                          - T_k(x) Lam[k+1]^{-1} H_k Gam[k+1]^{-1} ]    (k < d-1)
 //        B_{d-1}(x) = -alpha G_{d-1}(x)^{-1/(2m)} Lam[d-1]^{-1} E_{d-1}(x),
-//      which is R_{k-1}^{-1} (-alpha G_k^{-1/(4m)} A^_k) R_k with A^_k the
-//      Lemma 3.5 component: the weights and R factors of the projection cancel
-//      into r x r Gram inverses.
+//      i.e. R_{k-1}^{-1} (-alpha G_k^{-1/(4m)} A^_k) R_k with A^_k the Lemma 3.5
+//      component: weights and R factors cancel into r x r Gram inverses.
 //  (4) W_l in rank-2r TT form (rank bound of Section 3.1):
 //        C_0 = [B_0  T_0],  C_k = [[T_k, 0], [B_k, T_k]],  C_{d-1} = [[T_{d-1}], [T_{d-1} + B_{d-1}]].
 //  (5) T_{l+1} = SVD^tt_r(W_l), Algorithm 1 evaluated on the rank-2r TT:
-//      right Grams Psi[k] = sum_x C_k(x) Psi[k+1] C_k(x)^T; then for each bond
-//      k, with C'_k = S_{k-1} C_k:  N_k = sum_x C'_k(x)^T C'_k(x),
-//      Psi[k+1] = K K^T (eigendecomposition), K^T N_k K = V Sigma^2 V^T,
-//      P_k = K V_{:,1:r} Sigma^{-1},  new core T_k(x) = C'_k(x) P_k (left-
-//      orthogonal), S_k = P_k^T N_k.  The last core is S_{d-2} C_{d-1}(x).
-//      The top-r left singular vectors of (T^{<=k-1} (x) I)^T W^{<k>} are
-//      exactly those of L(C'_k) K, so this is Algorithm 1, not an approximation
-//      of it.
-// Every reduction over slices is split over blocks and summed in a fixed
-// order, so results are reproducible bit for bit.
+//      right Grams Psi[k] = sum_x C_k(x) Psi[k+1] C_k(x)^T; then bond by bond,
+//      with C'_k = S_{k-1} C_k and N_k = sum_x C'_k(x)^T C'_k(x), the top-r
+//      left singular vectors of (T^{<=k-1} (x) I)^T W^{<k>} = L(C'_k) C^{>=k+1}
+//      are L(C'_k) u for the dominant r-dimensional invariant subspace u of
+//      Psi[k+1] N_k (since M M^T L(C') u = L(C') Psi N u).  That subspace is
+//      found by subspace iteration started at the coordinates of the iterate's
+//      own part of the rank-2r cores, until the subspace moves by < 1e-14; the
+//      new core is T_k(x) = C'_k(x) P_k with P_k = U R^{-1}, R^T R = U^T N_k U,
+//      so it is left-orthogonal; S_k = P_k^T N_k; the last core is S_{d-2} C_{d-1}.
+//      This is Algorithm 1 itself, not an approximation of it.
+//
+// FP64 on GB300 has a 64-cycle dependent-FMA latency, so every factorization
+// with a long sequential chain runs in FP32 (Cholesky) and is lifted to FP64
+// accuracy by matrix products only (Newton-Schulz for inverses, a second-order
+// correction for the final normalisation).
+//
+// Reductions over slices are split over blocks; the last block to finish sums
+// the block partials in block order (deterministic) and runs the small
+// factorization that follows, so each stage is one launch.
 #include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "ctx.h"
@@ -38,149 +50,393 @@
 
 namespace {
 
-enum Op { OP_LAM = 0, OP_GAM = 1, OP_H = 2, OP_PSI = 3, OP_N = 4 };
+enum Op { OP_LAM = 0, OP_GAM = 1, OP_H = 2, OP_PSI = 3, OP_N = 4, OP_DAA = 5, OP_DAB = 6, OP_DBB = 7 };
+enum Post { POST_NONE = 0, POST_SMALL_PROJ = 1, POST_BOND = 2, POST_METRIC = 3 };
 
 struct Job {
   int op, k;
-  int nb;          // blocks
-  int dim;         // output is dim x dim
-  long long red;   // offset in P.red of the partials
-  int dst;         // offset in P.small of the result (-1: none)
+  int nb;            // reduction blocks
+  int rows, cols;    // output is rows x cols
+  long long red;     // offset in P.red of the partials
+  int dst;           // offset in P.small of the result
 };
 
-struct JobList {
+struct Stage {
   int njob;
+  int post, post_k;
+  int counter;       // index into P.counters
+  int which;         // metric stages: 0 truth, 1 previous iterate
+  int nmap;          // slice maps run by the first blocks
+  int map_k[2];
   Job job[TTC_MAXM + 4];
 };
 
-constexpr int kDenseThreads = 256;
+constexpr int kThreads = 256;
+constexpr int kMaxIter = 64;          // subspace iterations per bond
+constexpr double kMoveTol2 = 1e-28;   // squared subspace movement per basis vector at convergence
 
-__device__ __forceinline__ double wpow(const DevProb& P, int k, int x, double e) {
-  return pow(P.scal[SC_EPS] + P.s[k][x], e);
+// y = v^{-1/(2m)} by Newton's iteration for inverse roots,
+// y <- y (1 + (1 - v y^{2m}) / (2m)), started from the FP32 power (relative
+// error ~1e-7); each step squares the error, two steps reach FP64 rounding.
+// (No FP64 pow or division: FP64 has a 64-cycle latency on this GPU.)
+__device__ __forceinline__ double ipow_2m(double y, int two_m) {
+  double acc = 1.0, base = y;
+  for (int e = two_m; e > 0; e >>= 1) {
+    if (e & 1) acc *= base;
+    base *= base;
+  }
+  return acc;
+}
+__device__ __forceinline__ double inv_root(double v, int m) {
+  const int two_m = 2 * m;
+  double y = (double)powf((float)v, -1.0f / (float)two_m);
+  const double c = 1.0 / (double)two_m;
+  for (int it = 0; it < 2; ++it) y = y * fma(c, fma(-v, ipow_2m(y, two_m), 1.0), 1.0);
+  return y;
+}
+// G_k(x)^{+1/(2m)} (sign > 0) or G_k(x)^{-1/(2m)} (sign < 0)
+__device__ __forceinline__ double gpow(const DevProb& P, int k, int x, int sign) {
+  const double v = P.scal[SC_EPS] + P.s[k][x];
+  const double y = inv_root(v, P.m);            // v^{-1/(2m)}
+  return sign < 0 ? y : v * ipow_2m(y, 2 * P.m - 1);   // v^{1/(2m)} = v * y^{2m-1}
 }
 
-// one block: accumulates the contributions of slices blk, blk+nb, ... of one job
-__global__ void __launch_bounds__(kDenseThreads) k_reduce(const DevProb P, const JobList L) {
-  extern __shared__ __align__(16) double sm[];
-  int b = blockIdx.x, j = 0;
-  while (b >= L.job[j].nb) {
-    b -= L.job[j].nb;
-    ++j;
-  }
-  const Job J = L.job[j];
+// ---- per-slice contributions ------------------------------------------------
+__device__ void slice_contrib(const DevProb& P, const Stage& S, const Job& J, int x, double* acc, double* Y) {
   const int k = J.k, m = P.m;
-  const int dim = J.dim;
-  double* acc = sm;                 // dim x dim
-  double* Y = sm + dim * dim;       // up to 64 x 64
-  for (int i = threadIdx.x; i < dim * dim; i += blockDim.x) acc[i] = 0.0;
-  __syncthreads();
-  const int nk = P.n[k];
   const int ra = P.r[k], rb = P.r[k + 1];
-  const double invm2 = 1.0 / (2.0 * m);
-  for (int x = b; x < nk; x += J.nb) {
-    const double* T = P.core64[k] + (long long)x * ra * rb;
-    if (J.op == OP_LAM) {   // acc += w2 T^T (Lam T)
-      const double* Lam = P.small + P.off_lam[k];
-      blk_gemm<double>(ra, rb, ra, Lam, ra, false, T, rb, false, Y, rb, 1.0, false);
+  const double* T = P.core64[k] + (long long)x * ra * rb;
+  switch (J.op) {
+    case OP_LAM: {   // acc += w2 T^T (Lam T)
+      blk_gemm<double>(ra, rb, ra, P.small + P.off_lam[k], ra, false, T, rb, false, Y, rb, 1.0, false);
       __syncthreads();
-      blk_gemm<double>(rb, rb, ra, T, rb, true, Y, rb, false, acc, rb, wpow(P, k, x, invm2), true);
-    } else if (J.op == OP_GAM) {   // acc += w2 (T Gam) T^T
-      const double* Gam = P.small + P.off_gam[k + 1];
-      blk_gemm<double>(ra, rb, rb, T, rb, false, Gam, rb, false, Y, rb, 1.0, false);
+      blk_gemm<double>(rb, rb, ra, T, rb, true, Y, rb, false, acc, rb, gpow(P, k, x, +1), true);
+      break;
+    }
+    case OP_GAM: {   // acc += w2 (T Gam) T^T
+      blk_gemm<double>(ra, rb, rb, T, rb, false, P.small + P.off_gam[k + 1], rb, false, Y, rb, 1.0, false);
       __syncthreads();
-      blk_gemm<double>(ra, ra, rb, Y, rb, false, T, rb, true, acc, ra, wpow(P, k, x, invm2), true);
-    } else if (J.op == OP_H) {     // acc += T^T E
+      blk_gemm<double>(ra, ra, rb, Y, rb, false, T, rb, true, acc, ra, gpow(P, k, x, +1), true);
+      break;
+    }
+    case OP_H: {     // acc += T^T E
       const double* E = P.E[k] + (long long)x * ra * rb;
       blk_gemm<double>(rb, rb, ra, T, rb, true, E, rb, false, acc, rb, 1.0, true);
-    } else if (J.op == OP_PSI) {   // acc += (C Psi) C^T
+      break;
+    }
+    case OP_PSI: {   // acc += (C Psi) C^T
       const int qa = P.q[k], qb = P.q[k + 1];
       const double* C = P.C[k] + (long long)x * qa * qb;
-      const double* Psi = P.small + P.off_psi[k + 1];
-      blk_gemm<double>(qa, qb, qb, C, qb, false, Psi, qb, false, Y, qb, 1.0, false);
+      blk_gemm<double>(qa, qb, qb, C, qb, false, P.small + P.off_psi[k + 1], qb, false, Y, qb, 1.0, false);
       __syncthreads();
       blk_gemm<double>(qa, qa, qb, Y, qb, false, C, qb, true, acc, qa, 1.0, true);
-    } else {                       // OP_N: C' = S_{k-1} C ; acc += C'^T C'
+      break;
+    }
+    case OP_N: {     // C' = S_{k-1} C ; acc += C'^T C'
       const int qa = P.q[k], qb = P.q[k + 1];
       const double* C = P.C[k] + (long long)x * qa * qb;
       if (k == 0) {
         blk_gemm<double>(qb, qb, qa, C, qb, true, C, qb, false, acc, qb, 1.0, true);
       } else {
-        const double* S = P.small + P.off_sk[k - 1];   // r_k x q_k
-        blk_gemm<double>(ra, qb, qa, S, qa, false, C, qb, false, Y, qb, 1.0, false);
+        blk_gemm<double>(ra, qb, qa, P.small + P.off_sk[k - 1], qa, false, C, qb, false, Y, qb, 1.0, false);
         __syncthreads();
         blk_gemm<double>(qb, qb, ra, Y, qb, true, Y, qb, false, acc, qb, 1.0, true);
       }
+      break;
     }
-    __syncthreads();
+    default: {       // Gram sweep of the iterate A and another TT B
+      const int sa = S.which == 0 ? P.rt[k] : P.r[k], sb = S.which == 0 ? P.rt[k + 1] : P.r[k + 1];
+      const double* B = (S.which == 0 ? P.truth[k] : P.prev64[k]) + (long long)x * sa * sb;
+      if (J.op == OP_DAA) {
+        blk_gemm<double>(ra, rb, ra, P.small + P.off_mlam[0][k], ra, false, T, rb, false, Y, rb, 1.0, false);
+        __syncthreads();
+        blk_gemm<double>(rb, rb, ra, T, rb, true, Y, rb, false, acc, rb, 1.0, true);
+      } else if (J.op == OP_DAB) {
+        blk_gemm<double>(ra, sb, sa, P.small + P.off_mlam[1][k], sa, false, B, sb, false, Y, sb, 1.0, false);
+        __syncthreads();
+        blk_gemm<double>(rb, sb, ra, T, rb, true, Y, sb, false, acc, sb, 1.0, true);
+      } else {
+        blk_gemm<double>(sa, sb, sa, P.small + P.off_mlam[2][k], sa, false, B, sb, false, Y, sb, 1.0, false);
+        __syncthreads();
+        blk_gemm<double>(sb, sb, sa, B, sb, true, Y, sb, false, acc, sb, 1.0, true);
+      }
+      break;
+    }
   }
-  double* out = P.red + J.red + (long long)b * dim * dim;
-  for (int i = threadIdx.x; i < dim * dim; i += blockDim.x) out[i] = acc[i];
+  __syncthreads();
 }
 
-// sums the partials of every job in block order and stores the result
-__global__ void k_reduce_finish(const DevProb P, const JobList L) {
-  const Job J = L.job[blockIdx.x];
-  if (J.dst < 0) return;
-  const int dd = J.dim * J.dim;
-  for (int i = threadIdx.x; i < dd; i += blockDim.x) {
-    double a = 0.0;
-    for (int b = 0; b < J.nb; ++b) a += P.red[J.red + (long long)b * dd + i];
-    P.small[J.dst + i] = a;
-  }
-}
+// ---- small factorizations run by the last block ----------------------------
 
-__global__ void k_eps_alpha(const DevProb P) {
-  __shared__ double sh[kDenseThreads];
-  double v = 0.0;
-  for (int x = threadIdx.x; x < P.n[0]; x += blockDim.x) v += P.s[0][x];
-  double g2 = blk_sum(v, sh);
-  if (threadIdx.x == 0) {
-    double eps = P.scal[SC_EPS_FIXED] > 0.0 ? P.scal[SC_EPS_FIXED]
-                                            : fmax(P.scal[SC_EPS_REL] * g2 * P.inv_min_n, 1e-300);
-    double alpha = P.scal[SC_ALPHA_OVR] > 0.0 ? P.scal[SC_ALPHA_OVR] : P.scal[SC_ALPHA_SCALE] * sqrt(eps) / P.p;
-    P.scal[SC_G2] = g2;
-    P.scal[SC_EPS] = eps;
-    P.scal[SC_ALPHA] = alpha;
-    if (!isfinite(g2)) P.scal[SC_FLAGS] = (double)(((int)P.scal[SC_FLAGS]) | 1);
-  }
-}
-
-// Lam[k]^{-1}, Gam[k]^{-1} and Q_k = Lam[k+1]^{-1} H_k Gam[k+1]^{-1}
-__global__ void __launch_bounds__(kDenseThreads) k_small_proj(const DevProb P) {
-  extern __shared__ __align__(16) double sm[];
-  __shared__ int flag;
-  const int m = P.m;
-  double* A = sm;                       // 32 x 32
-  double* work = sm + TTC_MAXR * TTC_MAXR;
-  double* t1 = work + TTC_MAXR * TTC_MAXR;
+// Lam[k]^{-1}, Gam[k]^{-1} (k = 1..d-1), then Q_k = Lam[k+1]^{-1} H_k Gam[k+1]^{-1};
+// one warp per matrix.
+__device__ void post_small_proj(const DevProb& P, double* sm) {
+  const int m = P.m, warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+  int rmax = 1;
+  for (int k = 0; k <= m; ++k) rmax = max(rmax, P.r[k]);
+  const int nn = rmax * rmax;
+  // per warp: T (2 nn doubles), then L, Li (nn floats each)
+  double* T = sm + warp * 2 * nn;
+  float* Lf = reinterpret_cast<float*>(sm + nw * 2 * nn) + warp * 2 * nn;
+  float* Lif = Lf + nn;
   int bad = 0;
-  for (int k = 1; k < m; ++k) {       // Lam[k], k = 1..m-1 (Lam[0] = 1)
+  for (int j = warp; j < 2 * (m - 1); j += nw) {
+    const int k = 1 + (j >> 1);
     const int r = P.r[k];
-    for (int i = threadIdx.x; i < r * r; i += blockDim.x) A[i] = P.small[P.off_lam[k] + i];
-    __syncthreads();
-    bad |= blk_spd_inverse(A, r, work, &flag);
-    for (int i = threadIdx.x; i < r * r; i += blockDim.x) P.small[P.off_lami[k] + i] = A[i];
-    __syncthreads();
-    for (int i = threadIdx.x; i < r * r; i += blockDim.x) A[i] = P.small[P.off_gam[k] + i];
-    __syncthreads();
-    bad |= blk_spd_inverse(A, r, work, &flag);
-    for (int i = threadIdx.x; i < r * r; i += blockDim.x) P.small[P.off_gami[k] + i] = A[i];
-    __syncthreads();
+    const double* A = P.small + ((j & 1) ? P.off_gam[k] : P.off_lam[k]);
+    double* X = P.small + ((j & 1) ? P.off_gami[k] : P.off_lami[k]);
+    bad |= warp_spd_inverse(A, r, r, X, r, Lf, Lif, T);
   }
   if (threadIdx.x == 0) {
     P.small[P.off_lami[0]] = 1.0 / P.small[P.off_lam[0]];
     P.small[P.off_gami[m]] = 1.0 / P.small[P.off_gam[m]];
   }
+  __threadfence_block();
   __syncthreads();
-  for (int k = 0; k + 1 < m; ++k) {
+  for (int k = warp; k + 1 < m; k += nw) {
     const int r = P.r[k + 1];
-    blk_gemm<double>(r, r, r, P.small + P.off_lami[k + 1], r, false, P.small + P.off_h[k], r, false, t1, r, 1.0, false);
+    warp_gemm<double>(r, r, r, P.small + P.off_lami[k + 1], r, false, P.small + P.off_h[k], r, false, T, r, 1.0,
+                      false);
+    warp_gemm<double>(r, r, r, T, r, false, P.small + P.off_gami[k + 1], r, false, P.small + P.off_qm[k], r, 1.0,
+                      false);
+  }
+  unsigned any = __ballot_sync(0xffffffffu, bad);
+  if (lane == 0 && any) atomicOr(P.flags, 2u);
+}
+
+// Bond k of the retraction: from N_k (in P.small) and Psi[k+1], P_k and S_k.
+__device__ void post_bond(const DevProb& P, int k, double* sm) {
+  const int q = P.q[k + 1], r = P.r[k + 1];
+  const int tid = threadIdx.x;
+  double* N = sm;                 // q x q
+  double* A = N + q * q;          // q x q : Psi N
+  double* U = A + q * q;          // q x r
+  double* W = U + q * r;          // q x r
+  double* Z = W + q * r;          // q x r
+  double* G = Z + q * r;          // r x r
+  double* Bm = G + r * r;         // r x r
+  double* Rinv = Bm + r * r;      // r x r
+  double* red = Rinv + r * r;     // blockDim
+  float* Lf = reinterpret_cast<float*>(red + blockDim.x);
+  float* Lif = Lf + r * r;
+  __shared__ int bad;
+  for (int i = tid; i < q * q; i += blockDim.x) N[i] = P.small[P.off_nk[k] + i];
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  blk_gemm<double>(q, q, q, P.small + P.off_psi[k + 1], q, false, N, q, false, A, q, 1.0, false);
+  // start: the coordinates of the iterate's own part (last r of the 2r bond)
+  for (int i = tid; i < q * r; i += blockDim.x) {
+    int a = i / r, c = i - (i / r) * r;
+    U[i] = (a == q - r + c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  int it = 0;
+  for (; it < kMaxIter; ++it) {
+    blk_gemm<double>(q, r, q, A, q, false, U, r, false, W, r, 1.0, false);       // W = A U
     __syncthreads();
-    blk_gemm<double>(r, r, r, t1, r, false, P.small + P.off_gami[k + 1], r, false, P.small + P.off_qm[k], r, 1.0,
-                     false);
+    blk_gemm<double>(r, r, q, W, r, true, W, r, false, G, r, 1.0, false);        // G = W^T W
+    __syncthreads();
+    if (tid < 32) {
+      int b = warp_chol_inv32(G, r, r, Lf, Lif);
+      if (tid == 0 && b) bad = 1;
+    }
+    __syncthreads();
+    for (int i = tid; i < q * r; i += blockDim.x) {                               // Z = W L^{-T}
+      int a = i / r, c = i - (i / r) * r;
+      double acc = 0.0;
+      for (int t = 0; t <= c; ++t) acc = fma(W[a * r + t], (double)Lif[c * r + t], acc);
+      Z[i] = acc;
+    }
+    __syncthreads();
+    // FP64 orthonormality: E = Z^T Z - I, Z <- Z (I - E/2 + 3E^2/8)
+    blk_gemm<double>(r, r, q, Z, r, true, Z, r, false, Bm, r, 1.0, false);       // Bm = Z^T Z
+    __syncthreads();
+    for (int i = tid; i < r * r; i += blockDim.x) Bm[i] -= ((i / r) == (i % r)) ? 1.0 : 0.0;
+    __syncthreads();
+    blk_gemm<double>(r, r, r, Bm, r, false, Bm, r, false, Rinv, r, 0.375, false); // 3/8 E^2
+    __syncthreads();
+    for (int i = tid; i < r * r; i += blockDim.x) Rinv[i] += (((i / r) == (i % r)) ? 1.0 : 0.0) - 0.5 * Bm[i];
+    __syncthreads();
+    blk_gemm<double>(q, r, r, Z, r, false, Rinv, r, false, W, r, 1.0, false);    // W = Z F (orthonormal)
+    __syncthreads();
+    blk_gemm<double>(r, r, q, U, r, true, W, r, false, Bm, r, 1.0, false);       // Bm = U^T W
+    __syncthreads();
+    double dd = 0.0;
+    for (int i = tid; i < q * r; i += blockDim.x) {                               // movement W - U Bm
+      int a = i / r, c = i - (i / r) * r;
+      double acc = W[i];
+      for (int t = 0; t < r; ++t) acc = fma(-U[a * r + t], Bm[t * r + c], acc);
+      dd = fma(acc, acc, dd);
+    }
+    double mv = blk_sum(dd, red);
+    for (int i = tid; i < q * r; i += blockDim.x) U[i] = W[i];
+    __syncthreads();
+    if (mv <= kMoveTol2 * r) {
+      ++it;
+      break;
+    }
+  }
+  // normalisation: R^T R = U^T N U, R^{-1} from FP32 Cholesky plus a
+  // second-order FP64 correction (E = R0^{-T} G R0^{-1} - I,
+  // R^{-1} = R0^{-1} (I - E/2 + 3E^2/8))
+  blk_gemm<double>(q, r, q, N, q, false, U, r, false, W, r, 1.0, false);         // W = N U
+  __syncthreads();
+  blk_gemm<double>(r, r, q, U, r, true, W, r, false, G, r, 1.0, false);          // G = U^T N U
+  __syncthreads();
+  if (tid < 32) {
+    int b = warp_chol_inv32(G, r, r, Lf, Lif);
+    if (tid == 0 && b) bad = 1;
+  }
+  __syncthreads();
+  for (int i = tid; i < r * r; i += blockDim.x) {                                 // Rinv = L^{-T}
+    int a = i / r, c = i - (i / r) * r;
+    Rinv[i] = (double)Lif[c * r + a];
+  }
+  __syncthreads();
+  blk_gemm<double>(r, r, r, G, r, false, Rinv, r, false, Bm, r, 1.0, false);     // Bm = G Rinv
+  __syncthreads();
+  blk_gemm<double>(r, r, r, Rinv, r, true, Bm, r, false, Z, r, 1.0, false);      // Z = E + I
+  __syncthreads();
+  for (int i = tid; i < r * r; i += blockDim.x) Z[i] -= ((i / r) == (i % r)) ? 1.0 : 0.0;   // E
+  __syncthreads();
+  blk_gemm<double>(r, r, r, Z, r, false, Z, r, false, Bm, r, 0.375, false);      // Bm = 3/8 E^2
+  __syncthreads();
+  for (int i = tid; i < r * r; i += blockDim.x) Bm[i] += (((i / r) == (i % r)) ? 1.0 : 0.0) - 0.5 * Z[i];   // F
+  __syncthreads();
+  blk_gemm<double>(r, r, r, Rinv, r, false, Bm, r, false, G, r, 1.0, false);     // G = Rinv F
+  __syncthreads();
+  double* Pk = P.small + P.off_pk[k];
+  blk_gemm<double>(q, r, r, U, r, false, G, r, false, Pk, r, 1.0, false);        // P = U R^{-1}
+  __threadfence_block();
+  __syncthreads();
+  blk_gemm<double>(r, q, q, Pk, r, true, N, q, false, P.small + P.off_sk[k], q, 1.0, false);   // S = P^T N
+  if (tid == 0 && bad) atomicOr(P.flags, 2u);
+  if (tid == 0) P.scal[SC_SUBIT] = (k == 0 ? 0.0 : P.scal[SC_SUBIT]) + (double)it;
+}
+
+// new core k: T_k(x) = S_{k-1} C_k(x) P_k  (no P for the last core)
+__device__ void slice_map(const DevProb& P, int k, int x, double* Y) {
+  const int m = P.m;
+  const int qa = P.q[k], qb = P.q[k + 1];
+  const int ra = P.r[k], rb = P.r[k + 1];
+  const double* C = P.C[k] + (long long)x * qa * qb;
+  double* T = P.core64[k] + (long long)x * ra * rb;
+  float* T32 = P.core32p[k] + (long long)x * P.R * P.R;
+  double* T64 = P.core64p[k] + (long long)x * P.R * P.R;
+  const double* Cp = C;
+  if (k > 0) {
+    blk_gemm<double>(ra, qb, qa, P.small + P.off_sk[k - 1], qa, false, C, qb, false, Y, qb, 1.0, false);
+    __syncthreads();
+    Cp = Y;
+  }
+  if (k < m - 1) {
+    const double* Pk = P.small + P.off_pk[k];
+    for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
+      int a = i / rb, b = i - (i / rb) * rb;
+      double acc = 0.0;
+      for (int t = 0; t < qb; ++t) acc = fma(Cp[a * qb + t], Pk[t * rb + b], acc);
+      T[i] = acc;
+      T32[pad_idx(P, k, a, b)] = (float)acc;
+      T64[pad_idx(P, k, a, b)] = acc;
+    }
+  } else {
+    for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
+      int a = i / rb, b = i - (i / rb) * rb;
+      T[i] = Cp[i];
+      T32[pad_idx(P, k, a, b)] = (float)Cp[i];
+      T64[pad_idx(P, k, a, b)] = Cp[i];
+    }
+  }
+}
+
+// Sums the nb block partials of a job into P.small[dst] in a fixed order:
+// G = blockDim / outputs thread groups split the partials, each thread keeps
+// four independent register accumulators (loads pipeline, FP64 adds overlap),
+// and the groups are combined in group order through shared memory.
+__device__ void finish_job(const DevProb& P, const Job& J, double* sm) {
+  const int d2 = J.rows * J.cols;
+  const int groups = max(1, min((int)blockDim.x / max(d2, 1), 32));
+  const double* src = P.red + J.red;
+  for (int base = 0; base < d2; base += blockDim.x / groups) {
+    const int per = blockDim.x / groups;
+    const int g = threadIdx.x / per, i = base + (threadIdx.x - g * per);
+    double v = 0.0;
+    if (g < groups && i < d2) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int bb = g;
+      for (; bb + 3 * groups < J.nb; bb += 4 * groups) {
+        a0 += __ldcg(src + (long long)bb * d2 + i);
+        a1 += __ldcg(src + (long long)(bb + groups) * d2 + i);
+        a2 += __ldcg(src + (long long)(bb + 2 * groups) * d2 + i);
+        a3 += __ldcg(src + (long long)(bb + 3 * groups) * d2 + i);
+      }
+      for (; bb < J.nb; bb += groups) a0 += __ldcg(src + (long long)bb * d2 + i);
+      v = (a0 + a1) + (a2 + a3);
+    }
+    __syncthreads();
+    if (g < groups) sm[threadIdx.x] = v;
+    __syncthreads();
+    if (g == 0 && i < d2) {
+      double tot = 0.0;
+      for (int gg = 0; gg < groups; ++gg) tot += sm[gg * per + threadIdx.x];
+      P.small[J.dst + i] = tot;
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0 && bad) P.scal[SC_FLAGS] = (double)(((int)P.scal[SC_FLAGS]) | 2);
+}
+
+// ---- the stage kernel --------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_stage(const DevProb P, const Stage S) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ int am_last;
+  int b = blockIdx.x;
+  for (int i = 0; i < S.nmap; ++i) {     // slice maps first
+    const int k = S.map_k[i];
+    if (b < P.n[k]) {
+      slice_map(P, k, b, sm);
+      return;
+    }
+    b -= P.n[k];
+  }
+  int j = 0;
+  while (b >= S.job[j].nb) {
+    b -= S.job[j].nb;
+    ++j;
+  }
+  const Job J = S.job[j];
+  const int dd = J.rows * J.cols;
+  double* acc = sm;
+  double* Y = sm + dd;
+  for (int i = threadIdx.x; i < dd; i += blockDim.x) acc[i] = 0.0;
+  __syncthreads();
+  for (int x = b; x < P.n[J.k]; x += J.nb) slice_contrib(P, S, J, x, acc, Y);
+  double* out = P.red + J.red + (long long)b * dd;
+  for (int i = threadIdx.x; i < dd; i += blockDim.x) out[i] = acc[i];
+  // the last reduction block finishes the stage
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int total = 0;
+    for (int t = 0; t < S.njob; ++t) total += S.job[t].nb;
+    int prev = atomicAdd(P.counters + S.counter, 1);
+    am_last = (prev == total - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  for (int t = 0; t < S.njob; ++t) finish_job(P, S.job[t], sm);
+  if (threadIdx.x == 0) P.counters[S.counter] = 0;
+  __threadfence_block();
+  __syncthreads();
+  if (S.post == POST_SMALL_PROJ) {
+    post_small_proj(P, sm);
+  } else if (S.post == POST_BOND) {
+    post_bond(P, S.post_k, sm);
+  } else if (S.post == POST_METRIC && S.post_k == P.m - 1 && threadIdx.x == 0) {
+    double aa = P.small[P.off_mlam[0][P.m]], ab = P.small[P.off_mlam[1][P.m]], bbv = P.small[P.off_mlam[2][P.m]];
+    P.scal[SC_METRIC] = aa - 2.0 * ab + bbv;
+    P.scal[SC_NORM] = bbv;
+  }
 }
 
 // one block per slice (k, x): B_k(x) and the block core C_k(x)
@@ -195,29 +451,27 @@ __global__ void __launch_bounds__(128) k_build_C(const DevProb P) {
   const int x = blk, m = P.m;
   const int ra = P.r[k], rb = P.r[k + 1];
   const double alpha = P.scal[SC_ALPHA];
-  const double wi = wpow(P, k, x, -1.0 / (2.0 * m));
+  const double wi = gpow(P, k, x, -1);
   const double* T = P.core64[k] + (long long)x * ra * rb;
   const double* E = P.E[k] + (long long)x * ra * rb;
-  // t1 = Lam[k]^{-1} E
   blk_gemm<double>(ra, rb, ra, P.small + P.off_lami[k], ra, false, E, rb, false, t1, rb, 1.0, false);
   __syncthreads();
-  // B = -alpha wi t1 Gam[k+1]^{-1}
   blk_gemm<double>(ra, rb, rb, t1, rb, false, P.small + P.off_gami[k + 1], rb, false, B, rb, -alpha * wi, false);
   __syncthreads();
-  if (k + 1 < m) {   // B += alpha T Q_k
+  if (k + 1 < m) {
     blk_gemm<double>(ra, rb, rb, T, rb, false, P.small + P.off_qm[k], rb, false, B, rb, alpha, true);
     __syncthreads();
   }
   const int qa = P.q[k], qb = P.q[k + 1];
   double* C = P.C[k] + (long long)x * qa * qb;
   for (int i = threadIdx.x; i < qa * qb; i += blockDim.x) {
-    int a = i / qb, b = i % qb;
+    int a = i / qb, b = i - (i / qb) * qb;
     double v;
-    if (k == 0) {            // [B T]
+    if (k == 0) {
       v = (b < rb) ? B[a * rb + b] : T[a * rb + (b - rb)];
-    } else if (k == m - 1) { // [[T], [T + B]]
+    } else if (k == m - 1) {
       v = (a < ra) ? T[a * rb + b] : T[(a - ra) * rb + b] + B[(a - ra) * rb + b];
-    } else {                 // [[T, 0], [B, T]]
+    } else {
       if (a < ra)
         v = (b < rb) ? T[a * rb + b] : 0.0;
       else
@@ -227,96 +481,7 @@ __global__ void __launch_bounds__(128) k_build_C(const DevProb P) {
   }
 }
 
-// Truncated-SVD factor of bond k: N_k from partials, K from Psi[k+1],
-// eigen of K^T N_k K, P_k and S_k.
-__global__ void __launch_bounds__(kDenseThreads) k_sweep_factor(const DevProb P, int k, long long red, int nb) {
-  extern __shared__ __align__(16) double sm[];
-  const int q = P.q[k + 1], r = P.r[k + 1];
-  const int qq = q * q;
-  double* Nk = sm;
-  double* A = Nk + qq;
-  double* V = A + qq;
-  double* K = V + qq;
-  double* T1 = K + qq;
-  double* w = T1 + qq;
-  double* work = w + TTC_MAXQ;
-  for (int i = threadIdx.x; i < qq; i += blockDim.x) {
-    double a = 0.0;
-    for (int b = 0; b < nb; ++b) a += P.red[red + (long long)b * qq + i];
-    Nk[i] = a;
-    A[i] = P.small[P.off_psi[k + 1] + i];
-  }
-  __syncthreads();
-  blk_sym_eig(A, q, V, w, work);
-  for (int i = threadIdx.x; i < qq; i += blockDim.x) {
-    int c = i % q;
-    K[i] = V[i] * sqrt(fmax(w[c], 0.0));
-  }
-  __syncthreads();
-  blk_gemm<double>(q, q, q, Nk, q, false, K, q, false, T1, q, 1.0, false);   // N K
-  __syncthreads();
-  blk_gemm<double>(q, q, q, K, q, true, T1, q, false, A, q, 1.0, false);    // K^T N K
-  __syncthreads();
-  blk_sym_eig(A, q, V, w, work);
-  // P = K V[:, :r] diag(1/sigma)
-  __shared__ int lost;
-  if (threadIdx.x == 0) lost = 0;
-  __syncthreads();
-  double* Pk = P.small + P.off_pk[k];
-  double smax = sqrt(fmax(w[0], 0.0));
-  for (int i = threadIdx.x; i < q * r; i += blockDim.x) {
-    int a = i / r, c = i % r;
-    double sig = sqrt(fmax(w[c], 0.0));
-    double acc = 0.0;
-    for (int t = 0; t < q; ++t) acc = fma(K[a * q + t], V[t * q + c], acc);
-    if (sig > 1e-300 && sig > 1e-14 * smax) {
-      T1[i] = acc / sig;
-    } else {
-      T1[i] = 0.0;
-      lost = 1;
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < q * r; i += blockDim.x) Pk[i] = T1[i];
-  // S = P^T N  (r x q)
-  blk_gemm<double>(r, q, q, T1, r, true, Nk, q, false, P.small + P.off_sk[k], q, 1.0, false);
-  if (threadIdx.x == 0 && lost) P.scal[SC_FLAGS] = (double)(((int)P.scal[SC_FLAGS]) | 2);
-}
-
-// new core k: T_k(x) = S_{k-1} C_k(x) P_k  (P_k omitted for the last core)
-__global__ void __launch_bounds__(128) k_sweep_map(const DevProb P, int k) {
-  __shared__ double Y[TTC_MAXR * TTC_MAXQ];
-  const int x = blockIdx.x, m = P.m;
-  const int qa = P.q[k], qb = P.q[k + 1];
-  const int ra = P.r[k], rb = P.r[k + 1];
-  const double* C = P.C[k] + (long long)x * qa * qb;
-  double* T = P.core64[k] + (long long)x * ra * rb;
-  float* T32 = P.core32[k] + (long long)x * ra * rb;
-  const double* Cp = C;
-  if (k > 0) {
-    blk_gemm<double>(ra, qb, qa, P.small + P.off_sk[k - 1], qa, false, C, qb, false, Y, qb, 1.0, false);
-    __syncthreads();
-    Cp = Y;
-  }
-  if (k < m - 1) {
-    const double* Pk = P.small + P.off_pk[k];
-    for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
-      int a = i / rb, b = i % rb;
-      double acc = 0.0;
-      for (int t = 0; t < qb; ++t) acc = fma(Cp[a * qb + t], Pk[t * rb + b], acc);
-      T[i] = acc;
-      T32[i] = (float)acc;
-    }
-  } else {
-    for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
-      T[i] = Cp[i];
-      T32[i] = (float)Cp[i];
-    }
-  }
-}
-
 __global__ void k_copy_cores(const DevProb P, int to_prev) {
-  // grid-stride over all cores
   long long tot = 0;
   for (int k = 0; k < P.m; ++k) tot += (long long)P.n[k] * P.r[k] * P.r[k + 1];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
@@ -326,15 +491,20 @@ __global__ void k_copy_cores(const DevProb P, int to_prev) {
       o -= (long long)P.n[k] * P.r[k] * P.r[k + 1];
       ++k;
     }
-    if (to_prev)
+    if (to_prev) {
       P.prev64[k][o] = P.core64[k][o];
-    else
-      P.core32[k][o] = (float)P.core64[k][o];
+    } else {   // padded mirrors
+      const int ra = P.r[k], rb = P.r[k + 1];
+      const long long x = o / (ra * rb);
+      const int e = (int)(o - x * ra * rb), a = e / rb, b = e - (e / rb) * rb;
+      const long long d = x * P.R * P.R + pad_idx(P, k, a, b);
+      P.core32p[k][d] = (float)P.core64[k][o];
+      P.core64p[k][d] = P.core64[k][o];
+    }
   }
 }
 
-// ---- metrics: squared Frobenius distance between the iterate and another TT
-// Dense form (small d*): every entry is evaluated, in FP64.
+// ---- metrics: dense form for small d* (every entry, FP64) -------------------
 __global__ void k_dense_diff(const DevProb P, int which, long long dstar, double* part) {
   __shared__ double sh1[256];
   __shared__ double sh2[256];
@@ -346,7 +516,7 @@ __global__ void k_dense_diff(const DevProb P, int which, long long dstar, double
       xs[k] = (int)(t % P.n[k]);
       t /= P.n[k];
     }
-    double va[TTC_MAXQ], vb[TTC_MAXQ], tmp[TTC_MAXQ];
+    double va[TTC_MAXR], vb[TTC_MAXR], tmp[TTC_MAXR];
     va[0] = 1.0;
     vb[0] = 1.0;
     for (int k = 0; k < P.m; ++k) {
@@ -399,80 +569,37 @@ __global__ void k_dense_diff_finish(const DevProb P, const double* part, int nb)
   }
 }
 
-// Gram-sweep form (any d*): Lam_XY <- sum_x X_k(x)^T Lam_XY Y_k(x) for the pairs
-// (A,A), (A,B), (B,B); one block walks all slices of one core in order.
-__global__ void __launch_bounds__(kDenseThreads) k_gram_diff_step(const DevProb P, int which, int k, double* lam) {
-  extern __shared__ __align__(16) double sm[];
-  const int ra = P.r[k], rb = P.r[k + 1];
-  const int sa = which == 0 ? P.rt[k] : P.r[k], sb = which == 0 ? P.rt[k + 1] : P.r[k + 1];
-  const double* Bc = which == 0 ? P.truth[k] : P.prev64[k];
-  // lam layout: [AA: 64x64][AB: 64x64][BB: 64x64] (leading dim = current dims)
-  double* LAA = lam;
-  double* LAB = lam + TTC_MAXQ * TTC_MAXQ;
-  double* LBB = LAB + TTC_MAXQ * TTC_MAXQ;
-  double* nAA = sm;
-  double* nAB = nAA + TTC_MAXQ * TTC_MAXQ;
-  double* nBB = nAB + TTC_MAXQ * TTC_MAXQ;
-  double* Y = nBB + TTC_MAXQ * TTC_MAXQ;
-  for (int i = threadIdx.x; i < 3 * TTC_MAXQ * TTC_MAXQ; i += blockDim.x) sm[i] = 0.0;
-  __syncthreads();
-  for (int x = 0; x < P.n[k]; ++x) {
-    const double* A = P.core64[k] + (long long)x * ra * rb;
-    const double* B = Bc + (long long)x * sa * sb;
-    blk_gemm<double>(ra, rb, ra, LAA, ra, false, A, rb, false, Y, rb, 1.0, false);
-    __syncthreads();
-    blk_gemm<double>(rb, rb, ra, A, rb, true, Y, rb, false, nAA, rb, 1.0, true);
-    __syncthreads();
-    blk_gemm<double>(ra, sb, sa, LAB, sa, false, B, sb, false, Y, sb, 1.0, false);
-    __syncthreads();
-    blk_gemm<double>(rb, sb, ra, A, rb, true, Y, sb, false, nAB, sb, 1.0, true);
-    __syncthreads();
-    blk_gemm<double>(sa, sb, sa, LBB, sa, false, B, sb, false, Y, sb, 1.0, false);
-    __syncthreads();
-    blk_gemm<double>(sb, sb, sa, B, sb, true, Y, sb, false, nBB, sb, 1.0, true);
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < 3 * TTC_MAXQ * TTC_MAXQ; i += blockDim.x) lam[i] = sm[i];
-  __syncthreads();
-  if (k == P.m - 1 && threadIdx.x == 0) {
-    P.scal[SC_METRIC] = LAA[0] - 2.0 * LAB[0] + LBB[0];
-    P.scal[SC_NORM] = LBB[0];
-  }
-}
-
-__global__ void k_gram_diff_init(double* lam) {
-  for (int i = threadIdx.x; i < 3 * TTC_MAXQ * TTC_MAXQ; i += blockDim.x) lam[i] = 0.0;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    lam[0] = 1.0;
-    lam[TTC_MAXQ * TTC_MAXQ] = 1.0;
-    lam[2 * TTC_MAXQ * TTC_MAXQ] = 1.0;
-  }
-}
-
-// ---- host-side plan -------------------------------------------------------
+// ---- host-side plan ----------------------------------------------------------
 struct Plan {
-  std::vector<JobList> gram_steps;   // step j: Lam[j+1], Gam[m-1-j] (+ all H jobs at j = 0)
-  std::vector<JobList> psi_steps;    // k = m-1 .. 1
-  std::vector<JobList> n_steps;      // k = 0 .. m-2
-  long long red_total = 0;
+  std::vector<Stage> gram;       // Lam/Gam chains (+ H jobs in the first); the last runs small_proj
+  std::vector<Stage> psi;        // k = d-1 .. 1
+  std::vector<Stage> sweep;      // bond k (+ map of core k-1), then the final maps
+  std::vector<Stage> metric[2];  // Gram sweep of ||A - B||^2, which = 0 truth, 1 previous
+  size_t smem_stage = 0;
   double* metric_part = nullptr;
-  double* gram_lam = nullptr;
 };
 
-inline int nblocks_for(int nk) { return std::max(1, std::min(nk, 1024)); }
+std::map<const ttc_ctx*, Plan> g_plan_of;
+std::mutex g_plan_mu;
 
-}  // namespace
-
-// reduction plans, one per context
-#include <map>
-#include <mutex>
-static std::map<const ttc_ctx*, Plan> g_plan_of;
-static std::mutex g_plan_mu;
-static Plan& plan_of(const ttc_ctx* c) {
+Plan& plan_of(const ttc_ctx* c) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
   return g_plan_of[c];
 }
+
+inline int nblocks_for(int nk) { return std::max(1, std::min(nk, 1024)); }
+
+int launch_stage(ttc_ctx* c, const Stage& S, size_t smem) {
+  int nb = 0;
+  for (int i = 0; i < S.nmap; ++i) nb += (int)c->n[S.map_k[i]];
+  for (int j = 0; j < S.njob; ++j) nb += S.job[j].nb;
+  k_stage<<<nb, kThreads, smem, c->stream>>>(c->hp, S);
+  TTC_CUDA(cudaGetLastError());
+  c->nlaunch += 1;
+  return TTC_OK;
+}
+
+}  // namespace
 
 int ttc_alloc_dense(ttc_ctx* c) {
   DevProb& P = c->hp;
@@ -480,7 +607,6 @@ int ttc_alloc_dense(ttc_ctx* c) {
   P.q[0] = 1;
   P.q[m] = 1;
   for (int k = 1; k < m; ++k) P.q[k] = 2 * c->r[k];
-  // small matrices
   int off = 0;
   auto take = [&](int count) {
     int o = off;
@@ -494,6 +620,7 @@ int ttc_alloc_dense(ttc_ctx* c) {
     P.off_lami[k] = take(r * r);
     P.off_gami[k] = take(r * r);
     P.off_psi[k] = take(P.q[k] * P.q[k]);
+    for (int t = 0; t < 3; ++t) P.off_mlam[t][k] = take(TTC_MAXR * TTC_MAXR);
   }
   for (int k = 0; k < m; ++k) {
     int r = c->r[k + 1], q = P.q[k + 1];
@@ -507,11 +634,11 @@ int ttc_alloc_dense(ttc_ctx* c) {
   TTC_TRY(ttc_alloc(c, (void**)&small, sizeof(double) * (size_t)off, false));
   TTC_CUDA(cudaMemset(small, 0, sizeof(double) * (size_t)off));
   P.small = small;
-  // Lam[0] = Gam[m] = Psi[m] = [1]
   double one = 1.0;
   TTC_CUDA(cudaMemcpy(small + P.off_lam[0], &one, sizeof(double), cudaMemcpyHostToDevice));
   TTC_CUDA(cudaMemcpy(small + P.off_gam[m], &one, sizeof(double), cudaMemcpyHostToDevice));
   TTC_CUDA(cudaMemcpy(small + P.off_psi[m], &one, sizeof(double), cudaMemcpyHostToDevice));
+  for (int t = 0; t < 3; ++t) TTC_CUDA(cudaMemcpy(small + P.off_mlam[t][0], &one, sizeof(double), cudaMemcpyHostToDevice));
   for (int k = 0; k < m; ++k) {
     double* Ck = nullptr;
     TTC_TRY(ttc_alloc(c, (void**)&Ck, sizeof(double) * (size_t)c->n[k] * P.q[k] * P.q[k + 1], false));
@@ -524,72 +651,99 @@ int ttc_alloc_dense(ttc_ctx* c) {
   TTC_TRY(ttc_alloc(c, (void**)&scal, sizeof(double) * SC_COUNT, false));
   TTC_CUDA(cudaMemset(scal, 0, sizeof(double) * SC_COUNT));
   P.scal = scal;
+  P.flags = reinterpret_cast<unsigned*>(scal + SC_FLAGS);
+  int* counters = nullptr;
+  TTC_TRY(ttc_alloc(c, (void**)&counters, sizeof(int) * 128, false));
+  TTC_CUDA(cudaMemset(counters, 0, sizeof(int) * 128));
+  P.counters = counters;
 
-  // reduction plan
   Plan pl;
   long long red = 0;
-  auto mk = [&](int op, int k, int dim, int dst) {
+  int ctr = 1;   // counter 0 belongs to the slice reduction of the sampled pass
+  auto mk = [&](int op, int k, int rows, int cols, int dst) {
     Job J;
     J.op = op;
     J.k = k;
     J.nb = nblocks_for((int)c->n[k]);
-    J.dim = dim;
+    J.rows = rows;
+    J.cols = cols;
     J.red = red;
     J.dst = dst;
-    red += (long long)J.nb * dim * dim;
+    red += (long long)J.nb * rows * cols;
     return J;
   };
+  auto blank = [&]() {
+    Stage S;
+    memset(&S, 0, sizeof(S));
+    S.counter = ctr++;
+    return S;
+  };
   for (int j = 0; j + 1 < m; ++j) {
-    JobList L;
-    L.njob = 0;
-    L.job[L.njob++] = mk(OP_LAM, j, c->r[j + 1], P.off_lam[j + 1]);
+    Stage S = blank();
+    S.job[S.njob++] = mk(OP_LAM, j, c->r[j + 1], c->r[j + 1], P.off_lam[j + 1]);
     int kg = m - 1 - j;
-    L.job[L.njob++] = mk(OP_GAM, kg, c->r[kg], P.off_gam[kg]);
+    S.job[S.njob++] = mk(OP_GAM, kg, c->r[kg], c->r[kg], P.off_gam[kg]);
     if (j == 0)
-      for (int k = 0; k + 1 < m; ++k) L.job[L.njob++] = mk(OP_H, k, c->r[k + 1], P.off_h[k]);
-    pl.gram_steps.push_back(L);
+      for (int k = 0; k + 1 < m; ++k) S.job[S.njob++] = mk(OP_H, k, c->r[k + 1], c->r[k + 1], P.off_h[k]);
+    if (j + 2 == m) S.post = POST_SMALL_PROJ;
+    pl.gram.push_back(S);
   }
   for (int k = m - 1; k >= 1; --k) {
-    JobList L;
-    L.njob = 1;
-    L.job[0] = mk(OP_PSI, k, P.q[k], P.off_psi[k]);
-    pl.psi_steps.push_back(L);
+    Stage S = blank();
+    S.job[S.njob++] = mk(OP_PSI, k, P.q[k], P.q[k], P.off_psi[k]);
+    pl.psi.push_back(S);
   }
   for (int k = 0; k + 1 < m; ++k) {
-    JobList L;
-    L.njob = 1;
-    L.job[0] = mk(OP_N, k, P.q[k + 1], -1);
-    pl.n_steps.push_back(L);
+    Stage S = blank();
+    if (k > 0) {
+      S.nmap = 1;
+      S.map_k[0] = k - 1;
+    }
+    S.job[S.njob++] = mk(OP_N, k, P.q[k + 1], P.q[k + 1], P.off_nk[k]);
+    S.post = POST_BOND;
+    S.post_k = k;
+    pl.sweep.push_back(S);
   }
-  pl.red_total = red;
+  {
+    Stage S = blank();
+    S.nmap = 0;
+    S.map_k[S.nmap++] = m - 2;
+    S.map_k[S.nmap++] = m - 1;
+    pl.sweep.push_back(S);
+  }
+  for (int which = 0; which < 2; ++which) {
+    for (int k = 0; k < m; ++k) {
+      Stage S = blank();
+      S.which = which;
+      int ra = c->r[k + 1];
+      S.job[S.njob++] = mk(OP_DAA, k, ra, ra, P.off_mlam[0][k + 1]);
+      S.post = POST_METRIC;
+      S.post_k = k;
+      pl.metric[which].push_back(S);   // AB and BB jobs are added at launch (B's ranks)
+    }
+  }
+  if (ctr > 128) return TTC_EUNSUPPORTED;
+  long long metric_extra = 0;
+  for (int k = 0; k < m; ++k) metric_extra += 2LL * nblocks_for((int)c->n[k]) * TTC_MAXR * TTC_MAXR;
   double* redp = nullptr;
-  TTC_TRY(ttc_alloc(c, (void**)&redp, sizeof(double) * (size_t)std::max(red, 1LL), false));
+  TTC_TRY(ttc_alloc(c, (void**)&redp, sizeof(double) * (size_t)std::max(red + metric_extra, 1LL), false));
   P.red = redp;
+  P.red_metric = red;
   TTC_TRY(ttc_alloc(c, (void**)&pl.metric_part, sizeof(double) * 2 * 1024, false));
-  TTC_TRY(ttc_alloc(c, (void**)&pl.gram_lam, sizeof(double) * 3 * TTC_MAXQ * TTC_MAXQ, false));
+
+  int qmax = 1, rmax = 1;
+  for (int k = 0; k <= m; ++k) {
+    qmax = std::max(qmax, P.q[k]);
+    rmax = std::max(rmax, c->r[k]);
+  }
+  size_t red_need = sizeof(double) * (size_t)(2 * qmax * qmax);
+  red_need = std::max(red_need, sizeof(double) * (size_t)(2 * TTC_MAXR * TTC_MAXR));
+  size_t proj_need = sizeof(double) * (size_t)(8 * 2 * rmax * rmax) + sizeof(float) * (size_t)(8 * 2 * rmax * rmax);
+  size_t bond_need = sizeof(double) * (size_t)(2 * qmax * qmax + 3 * qmax * rmax + 3 * rmax * rmax + kThreads) +
+                     sizeof(float) * (size_t)(2 * rmax * rmax);
+  pl.smem_stage = std::max(red_need, std::max(proj_need, bond_need)) + 64;
+  TTC_CUDA(cudaFuncSetAttribute(k_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem_stage));
   plan_of(c) = pl;
-
-  // shared-memory opt-ins
-  int qmax = 1;
-  for (int k = 0; k <= m; ++k) qmax = std::max(qmax, P.q[k]);
-  size_t red_smem = sizeof(double) * 2 * TTC_MAXQ * TTC_MAXQ;
-  TTC_CUDA(cudaFuncSetAttribute(k_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red_smem));
-  size_t fac_smem = sizeof(double) * (5 * TTC_MAXQ * TTC_MAXQ + TTC_MAXQ + TTC_MAXQ * TTC_MAXQ + 4 * TTC_MAXQ + kDenseThreads);
-  TTC_CUDA(cudaFuncSetAttribute(k_sweep_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fac_smem));
-  size_t gd_smem = sizeof(double) * 4 * TTC_MAXQ * TTC_MAXQ;
-  TTC_CUDA(cudaFuncSetAttribute(k_gram_diff_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gd_smem));
-  return TTC_OK;
-}
-
-static int launch_jobs(ttc_ctx* c, const JobList& L) {
-  int nb = 0;
-  for (int j = 0; j < L.njob; ++j) nb += L.job[j].nb;
-  size_t smem = sizeof(double) * 2 * TTC_MAXQ * TTC_MAXQ;
-  k_reduce<<<nb, kDenseThreads, smem, c->stream>>>(c->hp, L);
-  TTC_CUDA(cudaGetLastError());
-  k_reduce_finish<<<L.njob, 256, 0, c->stream>>>(c->hp, L);
-  TTC_CUDA(cudaGetLastError());
-  c->nlaunch += 2;
   return TTC_OK;
 }
 
@@ -598,35 +752,14 @@ int ttc_launch_dense(ttc_ctx* c) {
   const int m = c->m;
   Plan& pl = plan_of(c);
   cudaStream_t st = c->stream;
-  k_eps_alpha<<<1, kDenseThreads, 0, st>>>(P);
-  TTC_CUDA(cudaGetLastError());
-  c->nlaunch += 1;
-  for (auto& L : pl.gram_steps) TTC_TRY(launch_jobs(c, L));
-  size_t sp_smem = sizeof(double) * 3 * TTC_MAXR * TTC_MAXR;
-  k_small_proj<<<1, kDenseThreads, sp_smem, st>>>(P);
-  TTC_CUDA(cudaGetLastError());
-  c->nlaunch += 1;
+  for (auto& S : pl.gram) TTC_TRY(launch_stage(c, S, pl.smem_stage));
   int nslices = 0;
   for (int k = 0; k < m; ++k) nslices += (int)c->n[k];
   k_build_C<<<nslices, 128, 0, st>>>(P);
   TTC_CUDA(cudaGetLastError());
   c->nlaunch += 1;
-  for (auto& L : pl.psi_steps) TTC_TRY(launch_jobs(c, L));
-  size_t fac_smem = sizeof(double) * (5 * TTC_MAXQ * TTC_MAXQ + TTC_MAXQ + TTC_MAXQ * TTC_MAXQ + 4 * TTC_MAXQ + kDenseThreads);
-  for (int k = 0; k + 1 < m; ++k) {
-    const JobList& L = pl.n_steps[k];
-    size_t smem = sizeof(double) * 2 * TTC_MAXQ * TTC_MAXQ;
-    k_reduce<<<L.job[0].nb, kDenseThreads, smem, st>>>(P, L);
-    TTC_CUDA(cudaGetLastError());
-    k_sweep_factor<<<1, kDenseThreads, fac_smem, st>>>(P, k, L.job[0].red, L.job[0].nb);
-    TTC_CUDA(cudaGetLastError());
-    k_sweep_map<<<(int)c->n[k], 128, 0, st>>>(P, k);
-    TTC_CUDA(cudaGetLastError());
-    c->nlaunch += 3;
-  }
-  k_sweep_map<<<(int)c->n[m - 1], 128, 0, st>>>(P, m - 1);
-  TTC_CUDA(cudaGetLastError());
-  c->nlaunch += 1;
+  for (auto& S : pl.psi) TTC_TRY(launch_stage(c, S, pl.smem_stage));
+  for (auto& S : pl.sweep) TTC_TRY(launch_stage(c, S, pl.smem_stage));
   return TTC_OK;
 }
 
@@ -657,13 +790,29 @@ int ttc_launch_metric(ttc_ctx* c, int which) {
     c->nlaunch += 2;
     return TTC_OK;
   }
-  k_gram_diff_init<<<1, 256, 0, c->stream>>>(pl.gram_lam);
-  size_t smem = sizeof(double) * 4 * TTC_MAXQ * TTC_MAXQ;
-  for (int k = 0; k < P.m; ++k) {
-    k_gram_diff_step<<<1, kDenseThreads, smem, c->stream>>>(P, which, k, pl.gram_lam);
-    TTC_CUDA(cudaGetLastError());
+  // Gram sweep: one stage per core with the AA, AB and BB jobs
+  const int m = P.m;
+  for (int k = 0; k < m; ++k) {
+    Stage S = pl.metric[which][k];
+    long long red = P.red_metric;
+    const int ra = P.r[k + 1];
+    const int sb = which == 0 ? P.rt[k + 1] : P.r[k + 1];
+    Job J = S.job[0];
+    J.op = OP_DAB;
+    J.rows = ra;
+    J.cols = sb;
+    J.red = red;
+    J.dst = P.off_mlam[1][k + 1];
+    red += (long long)J.nb * ra * sb;
+    S.job[S.njob++] = J;
+    J.op = OP_DBB;
+    J.rows = sb;
+    J.cols = sb;
+    J.red = red;
+    J.dst = P.off_mlam[2][k + 1];
+    S.job[S.njob++] = J;
+    TTC_TRY(launch_stage(c, S, pl.smem_stage));
   }
-  c->nlaunch += 1 + P.m;
   return TTC_OK;
 }
 

@@ -173,3 +173,102 @@ static __device__ void blk_sym_eig(double* A, int n, double* V, double* w, doubl
   }
   __syncthreads();
 }
+
+// ---------------------------------------------------------------------------
+// Warp-level helpers for the small factorizations.  GB300's FP64 pipe has a
+// 64-cycle dependent-FMA latency, so factorizations with long sequential
+// chains (Cholesky pivots, Jacobi rotations) run in FP32 and are brought to
+// FP64 accuracy by refinement steps that are matrix products only.
+// ---------------------------------------------------------------------------
+
+// One warp: lower Cholesky factor L of the SPD matrix A (FP64 input, n <= 32)
+// in FP32, and Li = L^{-1} (lower) in FP32.  L, Li: n*n floats (row-major).
+// Returns 1 if a pivot was not positive (it is then replaced by a tiny value).
+static __device__ int warp_chol_inv32(const double* A, int lda, int n, float* L, float* Li) {
+  const int lane = threadIdx.x & 31;
+  for (int idx = lane; idx < n * n; idx += 32) {
+    int i = idx / n, k = idx - (idx / n) * n;
+    L[idx] = (k <= i) ? (float)A[i * lda + k] : 0.f;
+  }
+  __syncwarp();
+  float scale = 0.f;
+  for (int i = 0; i < n; ++i) scale = fmaxf(scale, fabsf(L[i * n + i]));
+  int bad = 0;
+  for (int j = 0; j < n; ++j) {
+    float d = L[j * n + j];
+    if (!(d > 1e-30f * scale + 1e-38f)) {
+      d = 1e-30f * scale + 1e-38f;
+      bad = 1;
+    }
+    float ljj = sqrtf(d), inv = 1.f / ljj;
+    __syncwarp();
+    for (int i = j + lane; i < n; i += 32) L[i * n + j] = (i == j) ? ljj : L[i * n + j] * inv;
+    __syncwarp();
+    for (int i = j + 1 + lane; i < n; i += 32) {
+      float lij = L[i * n + j];
+      for (int k = j + 1; k <= i; ++k) L[i * n + k] = fmaf(-lij, L[k * n + j], L[i * n + k]);
+    }
+    __syncwarp();
+  }
+  for (int c = lane; c < n; c += 32) {
+    for (int i = 0; i < c; ++i) Li[i * n + c] = 0.f;
+    Li[c * n + c] = 1.f / L[c * n + c];
+    for (int i = c + 1; i < n; ++i) {
+      float acc = 0.f;
+      for (int k = c; k < i; ++k) acc = fmaf(L[i * n + k], Li[k * n + c], acc);
+      Li[i * n + c] = -acc / L[i * n + i];
+    }
+  }
+  __syncwarp();
+  return bad;
+}
+
+// C (M x N, ldc) = alpha op(A) op(B) (+ C when accumulate) by one warp.
+template <typename T>
+__device__ void warp_gemm(int M, int N, int K, const T* A, int lda, bool ta, const T* B, int ldb, bool tb, T* C,
+                          int ldc, T alpha, bool accumulate) {
+  const int lane = threadIdx.x & 31;
+  for (int idx = lane; idx < M * N; idx += 32) {
+    int i = idx / N, j = idx - (idx / N) * N;
+    T acc = 0;
+    for (int k = 0; k < K; ++k) {
+      T a = ta ? A[k * lda + i] : A[i * lda + k];
+      T b = tb ? B[j * ldb + k] : B[k * ldb + j];
+      acc = fma(a, b, acc);
+    }
+    C[i * ldc + j] = accumulate ? fma(alpha, acc, C[i * ldc + j]) : alpha * acc;
+  }
+  __syncwarp();
+}
+
+// One warp: X = A^{-1} for SPD A (n <= 32), FP64 result.  X0 = L^{-T} L^{-1}
+// from the FP32 Cholesky, then two Newton-Schulz steps X <- X + X (I - A X)
+// in FP64 (each squares the relative error: 1e-7 kappa -> FP64 rounding).
+// Scratch: L, Li (n*n floats each), T (2*n*n doubles).  Returns the pivot flag.
+static __device__ int warp_spd_inverse(const double* A, int lda, int n, double* X, int ldx, float* L, float* Li,
+                                       double* T) {
+  const int lane = threadIdx.x & 31;
+  int bad = warp_chol_inv32(A, lda, n, L, Li);
+  for (int idx = lane; idx < n * n; idx += 32) {
+    int i = idx / n, j = idx - (idx / n) * n;
+    int k0 = i > j ? i : j;
+    double acc = 0.0;
+    for (int k = k0; k < n; ++k) acc = fma((double)Li[k * n + i], (double)Li[k * n + j], acc);
+    X[i * ldx + j] = acc;
+  }
+  __syncwarp();
+  double* T1 = T;
+  double* T2 = T + n * n;
+  for (int it = 0; it < 2; ++it) {
+    warp_gemm<double>(n, n, n, A, lda, false, X, ldx, false, T1, n, -1.0, false);   // T1 = -A X
+    for (int i = lane; i < n; i += 32) T1[i * n + i] += 1.0;                          // T1 = I - A X
+    __syncwarp();
+    warp_gemm<double>(n, n, n, X, ldx, false, T1, n, false, T2, n, 1.0, false);      // T2 = X T1
+    for (int idx = lane; idx < n * n; idx += 32) {
+      int i = idx / n, j = idx - (idx / n) * n;
+      X[i * ldx + j] += T2[idx];
+    }
+    __syncwarp();
+  }
+  return bad;
+}

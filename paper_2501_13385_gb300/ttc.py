@@ -43,7 +43,8 @@ class Options(C.Structure):
 
 
 class StepInfo(C.Structure):
-    _fields_ = [("eps", C.c_double), ("alpha", C.c_double), ("res_norm", C.c_double), ("precision_used", C.c_int)]
+    _fields_ = [("eps", C.c_double), ("alpha", C.c_double), ("res_norm", C.c_double), ("precision_used", C.c_int),
+                ("subspace_iters", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -211,7 +212,7 @@ class Context:
         info = StepInfo()
         _check(lib().ttc_step(self._h, float(alpha), C.byref(info)), "ttc_step")
         return {"eps": info.eps, "alpha": info.alpha, "res_norm": info.res_norm,
-                "precision_used": info.precision_used}
+                "precision_used": info.precision_used, "subspace_iters": info.subspace_iters}
 
     def solve(self, raise_on_notconv: bool = False) -> dict:
         info = SolveInfo()

@@ -5,9 +5,11 @@ Workload: the orthogonal-cubic tensor-completion problem, order 3, 200 per
 mode, TT-ranks (1,5,5,1), 5% of entries observed (|Omega| = 400 000),
 noiseless; synthetic, seeded.  A step is one PRGD iteration (sampled pass over
 Omega, weights, weighted tangent projection, rank-2r assembly, TT-rounding
-retraction) in the MIXED mode (FP32 sampled pass, FP64 dense stages), with all
-inputs resident in device memory.  L2 is flushed (256 MB write) between timed
-steps, outside the timed brackets.
+retraction) in the MIXED mode (FP32 sampled pass, FP64 dense stages) of a
+batch of B independent such problems (default 32, seeds differ), launched as
+one CUDA graph, with all inputs resident in device memory.  The batch's
+inputs are larger than L2; for small batches L2 is flushed (256 MB write)
+between timed steps, outside the timed brackets.
 
 Prints ONE JSON line.  `--impl reference` times the FP64 CPU oracle on the
 same workload instead (the reference arm; rank 0 only).
@@ -43,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-solves", type=int, default=3)
     ap.add_argument("--e2e-iters", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=32,
+                    help="independent problems per step (one CUDA graph launch); 1 = a single problem")
     return ap.parse_args()
 
 
@@ -161,28 +165,31 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def algorithmic_bytes_per_launch(P, W=1):
-    """Bytes the sampled pass must move per launch: for every mode k, every
-    entry's packed code (4W bytes) and FP32 value (4 bytes), plus one FP32
-    partial (1 + r_k r_{k+1} values) written per chunk of 128 entries."""
+def algorithmic_bytes_per_launch(P, W=1, chunk=1024):
+    """Bytes the sampled pass must move per launch for one problem: for every
+    mode k, every entry's packed code (4W bytes) and FP32 value (4 bytes),
+    plus one FP32 partial (1 + r_k r_{k+1} values) written per chunk of
+    `chunk` entries of a slice.  Core slices are L2/L1-resident and not
+    counted."""
     import numpy as np
     total = 0
     for k in range(P.m):
         counts = np.bincount(P.idx[:, k], minlength=P.n[k])
-        chunks = int(np.sum((counts + 127) // 128))
+        chunks = int(np.sum((counts + chunk - 1) // chunk))
         total += P.N * (4 * W + 4) + chunks * (1 + P.r[k] * P.r[k + 1]) * 4
     return total
 
 
-def load_traffic(kernel_file):
+def load_traffic(kernel_file, batch):
     """dram bytes per launch of the dominant kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+    summary, if it was taken on the current kernel source and batch size."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))
         src = open(kernel_file, "rb").read()
-        if rec.get("source_sha1") == hashlib.sha1(src).hexdigest() and rec.get("workload") == WORKLOAD["workload"]:
+        if (rec.get("source_sha1") == hashlib.sha1(src).hexdigest() and rec.get("workload") == WORKLOAD["workload"]
+                and rec.get("batch") == batch):
             return rec.get("dram_bytes_per_launch")
     except Exception:
         pass
@@ -206,63 +213,72 @@ def ttc_arm(args):
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    P = w.orthogonal_cubic(rank)
-    ctx = ttc.Context(P.n, P.r, stream=stream.cuda_stream, precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_NONE)
-    ctx.set_observations(P.idx, P.y)
-    ctx.set_cores(P.init)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    B = max(1, args.batch)
+    probs = [w.orthogonal_cubic(rank * B + i) for i in range(B)]
+    N = probs[0].N
+
+    def make_ctx(P, prec, stop=ttc.STOP_NONE, **kw):
+        c = ttc.Context(P.n, P.r, precision=prec, stop_rule=stop, **kw)
+        c.set_observations(P.idx, P.y)
+        c.set_cores(P.init)
+        return c
+
+    ctxs = [make_ctx(P, ttc.PREC_MIXED) for P in probs]
+    batch = ttc.Batch(ctxs, stream=stream.cuda_stream)
+    flush = None
+    l2_note = "inputs larger than L2 (no flush)"
+    if B * algorithmic_bytes_per_launch(probs[0]) < 4 * 129 * 2 ** 20:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        l2_note = "flushed between timed steps (256 MB write)"
 
     for _ in range(args.warmup):
-        ctx.step_async()
-    torch.cuda.synchronize()
-    ctx.profile_enable(True)
-    ctx.step_async()                      # first profiled iteration recaptures the graph
-    torch.cuda.synchronize()
-    ctx.profile_read(reset=True)
+        batch.step()
+    batch.sync()
+    batch.profile_enable(True)
+    batch.step()                          # recaptures with the timing event nodes
+    batch.sync()
+    batch.profile_read(reset=True)
 
     K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    launches0 = ctx.launch_count()
+    launches0 = batch.launch_count()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for i in range(K):
             ev[i][0].record(stream)
-            ctx.step_async()
+            batch.step()
             ev[i][1].record(stream)
-            flush.zero_()
+            if flush is not None:
+                flush.zero_()
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    launches = ctx.launch_count() - launches0
+    launches = batch.launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    kern_ms, kern_n = ctx.profile_read(reset=True)
-    ctx.profile_enable(False)
+    kern_ms, kern_n = batch.profile_read(reset=True)
+    batch.close()
+    for c in ctxs:
+        c.close()
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / K
-    value = world * P.N * K / (total_ms / 1e3)
+    value = world * B * N * K / (total_ms / 1e3)
 
-    # iterations to rel.err <= 1e-6 (vs T*), mixed and plain FP64, and their time
+    # iterations and time to rel.err <= 1e-6 (vs T*) for one problem, mixed and plain FP64
+    P = probs[0]
     to_tol = {}
     for name, prec in (("mixed", ttc.PREC_MIXED), ("fp64", ttc.PREC_FP64)):
-        with ttc.Context(P.n, P.r, stream=stream.cuda_stream, precision=prec, stop_rule=ttc.STOP_RELERR,
-                         tol=1e-6, max_iter=200) as c2:
-            c2.set_observations(P.idx, P.y)
-            c2.set_cores(P.init)
+        with make_ctx(P, prec, ttc.STOP_RELERR, tol=1e-6, max_iter=200) as c2:
             c2.set_truth(P.truth)
             res = c2.solve()
         iters = res["iters"]
-        with ttc.Context(P.n, P.r, stream=stream.cuda_stream, precision=prec, stop_rule=ttc.STOP_NONE,
-                         max_iter=iters) as c3:
-            c3.set_observations(P.idx, P.y)
-            c3.set_cores(P.init)
-            c3.step_async()
-            torch.cuda.synchronize()
+        with make_ctx(P, prec, ttc.STOP_NONE, max_iter=iters) as c3:
+            c3.solve()                     # capture the graphs
             c3.set_cores(P.init)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -272,30 +288,37 @@ def ttc_arm(args):
         to_tol[name] = {"iters": iters, "converged": res["converged"], "ms": 1e3 * dt,
                         "polish_iter": res["polish_iter"]}
 
-    # end to end through the public API from pinned host buffers
-    idx_h = torch.from_numpy(np.ascontiguousarray(P.idx, dtype=np.int32)).pin_memory().numpy()
-    y_h = torch.from_numpy(np.ascontiguousarray(P.y)).pin_memory().numpy()
-    init_h = [torch.from_numpy(np.ascontiguousarray(c)).pin_memory().numpy() for c in P.init]
+    # end to end through the public API from pinned host buffers: every step
+    # copies all B problems' observations and starting cores in, runs
+    # e2e_iters batched iterations and reads all cores back
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    idx_h = [pin(P.idx.astype(np.int32)) for P in probs]
+    y_h = [pin(P.y) for P in probs]
+    init_h = [[pin(c) for c in P.init] for P in probs]
     e2e_ms = []
     out_bytes = 0
-    with ttc.Context(P.n, P.r, stream=stream.cuda_stream, precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_NONE,
-                     max_iter=args.e2e_iters) as ce:
-        ce.set_observations(idx_h, y_h)       # warm-up call (graph capture, allocations)
-        ce.set_cores(init_h)
-        ce.solve()
-        for _ in range(args.e2e_solves):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ce.set_observations(idx_h, y_h)
-            ce.set_cores(init_h)
-            ce.solve()
-            res_cores = ce.get_cores()
-            e2e_ms.append(1e3 * (time.perf_counter() - t0))
-            out_bytes = sum(c.nbytes for c in res_cores)
-    h2d = idx_h.nbytes + y_h.nbytes + sum(c.nbytes for c in init_h)
-    e2e_val = world * P.N * args.e2e_iters / (statistics.mean(e2e_ms) / 1e3)
+    ectx = [ttc.Context(P.n, P.r, precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_NONE) for P in probs]
+    for rep in range(args.e2e_solves + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c, ih, yh, ch in zip(ectx, idx_h, y_h, init_h):
+            c.set_observations(ih, yh)
+            c.set_cores(ch)
+        with ttc.Batch(ectx) as eb:
+            for _ in range(args.e2e_iters):
+                eb.step()
+            eb.sync()
+        res_cores = [c.get_cores() for c in ectx]
+        dt = 1e3 * (time.perf_counter() - t0)
+        if rep > 0:                         # the first round captures graphs
+            e2e_ms.append(dt)
+        out_bytes = sum(a.nbytes for cs in res_cores for a in cs)
+    for c in ectx:
+        c.close()
+    h2d = sum(a.nbytes for a in idx_h) + sum(a.nbytes for a in y_h) + sum(a.nbytes for cs in init_h for a in cs)
+    e2e_val = world * B * N * args.e2e_iters / (statistics.mean(e2e_ms) / 1e3)
 
-    # roofline of the dominant kernel (the sampled pass)
+    # roofline of the dominant kernel: the batched sampled pass, one launch per step
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -304,12 +327,12 @@ def ttc_arm(args):
     peak = peaks.get("hbm_gbs")
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
-    alg = algorithmic_bytes_per_launch(P)
+    alg = sum(algorithmic_bytes_per_launch(P) for P in probs)
     kern_avg_ms = kern_ms / max(kern_n, 1)
     achieved = alg / (kern_avg_ms / 1e3) / 1e9
-    traffic = load_traffic(os.path.join(ROOT, "paper_2501_13385_gb300", "csrc", "omega_pass.cu"))
+    traffic = load_traffic(os.path.join(ROOT, "paper_2501_13385_gb300", "csrc", "omega_pass.cu"), B)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "k_sample_project<float,8>", "kernel_ms": kern_avg_ms,
+            "traffic": traffic, "kernel": "k_sample_project_batch<float,8>", "kernel_ms": kern_avg_ms,
             "launches_timed": kern_n, "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
 
     cpu = None
@@ -317,28 +340,28 @@ def ttc_arm(args):
         r = run_oracle(seed=0, warm=1, steps=100, budget_s=15.0, bounded=True)
         t = r["times"]
         cpu = {"value": r["N"] / statistics.mean(t), "unit": "Ω-entries/s", "cores": 1, "kind": "oracle",
-               "sample": f"{len(t)} PRGD iterations of the full workload, ~15 s of one host core"}
+               "sample": f"{len(t)} PRGD iterations of one orthogonal_cubic problem, ~15 s of one host core"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Ω-entries/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 sampled pass + f64 dense stages", "data": "synthetic",
-            "config": dict(WORKLOAD, precision="mixed", l2="flushed between timed steps (256 MB write)",
+            "config": dict(WORKLOAD, batch=B, precision="mixed", l2=l2_note,
                            parallelism="replicas" if world > 1 else "single GPU"),
             "iters_per_s": 1e3 / ms_per_step,
+            "problem_iters_per_s": B * 1e3 / ms_per_step,
             "step_ms_p50": statistics.median(step_ms), "step_ms_p99": sorted(step_ms)[max(0, int(0.99 * K) - 1)],
             "to_rel_err_1e-6": to_tol,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "Ω-entries/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": out_bytes, "iters_per_solve": args.e2e_iters,
-                    "ms_per_solve": statistics.mean(e2e_ms)},
+                    "d2h_bytes_per_step": out_bytes, "iters_per_step": args.e2e_iters,
+                    "ms_per_step": statistics.mean(e2e_ms)},
             "gpu_launches": launches,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -177,6 +177,33 @@ int ttc_launch_count(ttc_ctx* ctx, int64_t* launches);
 /* Device bytes held by the context. */
 int ttc_device_bytes(ttc_ctx* ctx, int64_t* bytes);
 
+/* ---- batches -------------------------------------------------------------
+ * A batch steps many independent contexts together: one call enqueues one
+ * PRGD iteration of every member as ONE CUDA graph launch.  The sampled pass
+ * of all members that share a precision and rank bucket runs as one kernel
+ * launch (blocks mapped to (member, chunk)), and the members' dense stages run
+ * as parallel branches of the graph on their own streams.  Each member
+ * computes exactly what it computes when stepped alone (bitwise).
+ * Members must have observations and cores set, must not be stepped on their
+ * own while the batch is in use, and must not change their observations or
+ * truth afterwards (create a new batch instead).  The batch does not own the
+ * members; destroy the batch before them. */
+typedef struct ttc_batch ttc_batch;
+int ttc_batch_create(ttc_batch** out, ttc_ctx* const* members, int count, void* cuda_stream);
+/* Enqueue one iteration of every member on the batch's stream (no wait,
+ * except with profiling on, see below). */
+int ttc_batch_step(ttc_batch* b);
+/* Wait for all work enqueued by the batch. */
+int ttc_batch_sync(ttc_batch* b);
+/* Profiling: the batched sampled-pass launch(es) of every step are bracketed
+ * by events (graph event-record nodes); each step then waits for the end
+ * event and adds the duration. */
+int ttc_batch_profile_enable(ttc_batch* b, int on);
+int ttc_batch_profile_read(ttc_batch* b, double* ms, int64_t* count, int reset);
+/* Kernels launched by the batch so far (all graph kernel nodes of each step). */
+int ttc_batch_launch_count(ttc_batch* b, int64_t* launches);
+void ttc_batch_destroy(ttc_batch* b);
+
 /* Allocation-free squared Frobenius distance of two tensor trains (the paper
  * has no counterpart of this call).  For callers that may not allocate
  * device memory themselves, e.g. a real-time loop with a fixed memory budget

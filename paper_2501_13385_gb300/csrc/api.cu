@@ -291,6 +291,14 @@ int ttc_set_observations(ttc_ctx* c, int64_t N, const int32_t* idx, const double
   P.p = (double)N / dstar;
   int s = ttc_build_layout(c, idx, y);
   if (s != TTC_OK) return s;
+  ttc_plan_tables(c);
+  P.tab32 = nullptr;
+  P.tab64 = nullptr;
+  if (P.tab_total > 0) {
+    size_t cnt = (size_t)P.tab_total * c->rank_bucket;
+    TTC_TRY(ttc_alloc(c, (void**)&P.tab32, sizeof(float) * cnt, true));
+    TTC_TRY(ttc_alloc(c, (void**)&P.tab64, sizeof(double) * cnt, true));
+  }
   c->have_obs = true;
   c->eps_set = false;
   TTC_TRY(set_scalar(c, SC_EPS_FIXED, 0.0));

@@ -1,0 +1,292 @@
+// Batches: many independent completion problems stepped by one CUDA graph.
+// One PRGD iteration of every member is one graph launch: the sampled pass
+// of all members sharing a precision and rank bucket is ONE launch of the
+// batched kernel (blocks mapped to (problem, chunk) through a prefix array),
+// followed by the batched slice reduction; the dense stages of the members
+// then run as parallel branches of the graph, each on its member's stream.
+// Every member computes exactly what it computes alone (same kernels, same
+// block decomposition), so results are bitwise identical alone or in a batch.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ctx.h"
+
+struct ttc_batch {
+  std::vector<ttc_ctx*> members;
+  std::vector<int> prec_at_capture;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  struct Group {
+    BatchGroup g;
+    DevProb* probs = nullptr;
+    int* pass_base = nullptr;
+    int* seg_base = nullptr;
+    long long* tab_base = nullptr;
+    std::vector<int> idx;
+  };
+  std::vector<Group> groups;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels_per_step = 0;
+  long long nlaunch = 0;
+  bool prof = false;
+  cudaEvent_t ev_beg = nullptr, ev_end = nullptr;
+  double prof_ms = 0.0;
+  long long prof_count = 0;
+};
+
+namespace {
+
+void free_groups(ttc_batch* b) {
+  for (auto& G : b->groups) {
+    cudaFree(G.probs);
+    cudaFree(G.pass_base);
+    cudaFree(G.seg_base);
+    cudaFree(G.tab_base);
+  }
+  b->groups.clear();
+}
+
+int build_groups(ttc_batch* b) {
+  free_groups(b);
+  std::vector<std::pair<int, int>> keys;   // (prec, R)
+  for (auto* c : b->members) {
+    int prec = c->cur_prec == TTC_PREC_FP64 ? TTC_PREC_FP64 : TTC_PREC_FP32;
+    std::pair<int, int> key(prec, c->rank_bucket);
+    if (std::find(keys.begin(), keys.end(), key) == keys.end()) keys.push_back(key);
+  }
+  for (auto& key : keys) {
+    ttc_batch::Group G;
+    std::vector<DevProb> descs;
+    std::vector<int> pb(1, 0), sb(1, 0);
+    std::vector<long long> tb(1, 0);
+    for (int i = 0; i < (int)b->members.size(); ++i) {
+      ttc_ctx* c = b->members[i];
+      int prec = c->cur_prec == TTC_PREC_FP64 ? TTC_PREC_FP64 : TTC_PREC_FP32;
+      if (prec != key.first || c->rank_bucket != key.second) continue;
+      G.idx.push_back(i);
+      descs.push_back(c->hp);
+      pb.push_back(pb.back() + c->hp.chunk_base[c->m]);
+      int nseg = 0;
+      for (int k = 0; k < c->m; ++k) nseg += c->hp.n[k];
+      sb.push_back(sb.back() + nseg);
+      tb.push_back(tb.back() + c->hp.tab_total);
+    }
+    cudaError_t e = cudaMalloc(&G.probs, sizeof(DevProb) * descs.size());
+    if (e == cudaSuccess) e = cudaMalloc(&G.pass_base, sizeof(int) * pb.size());
+    if (e == cudaSuccess) e = cudaMalloc(&G.seg_base, sizeof(int) * sb.size());
+    if (e == cudaSuccess) e = cudaMemcpy(G.probs, descs.data(), sizeof(DevProb) * descs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(G.pass_base, pb.data(), sizeof(int) * pb.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(G.seg_base, sb.data(), sizeof(int) * sb.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&G.tab_base, sizeof(long long) * tb.size());
+    if (e == cudaSuccess) e = cudaMemcpy(G.tab_base, tb.data(), sizeof(long long) * tb.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      ttc_record_cuda_error(e);
+      b->groups.push_back(G);
+      free_groups(b);
+      return e == cudaErrorMemoryAllocation ? TTC_ENOMEM : TTC_ECUDA;
+    }
+    G.g.prec = key.first;
+    G.g.R = key.second;
+    G.g.nprob = (int)descs.size();
+    G.g.probs = G.probs;
+    G.g.pass_base = G.pass_base;
+    G.g.seg_base = G.seg_base;
+    G.g.tab_base = G.tab_base;
+    G.g.pass_blocks = pb.back();
+    G.g.seg_blocks = sb.back();
+    G.g.tab_rows = tb.back();
+    b->groups.push_back(G);
+  }
+  return TTC_OK;
+}
+
+int capture(ttc_batch* b) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  TTC_TRY(build_groups(b));
+  b->prec_at_capture.clear();
+  for (auto* c : b->members) b->prec_at_capture.push_back(c->cur_prec);
+  std::vector<long long> before;
+  for (auto* c : b->members) before.push_back(c->nlaunch);
+  cudaGraph_t g = nullptr;
+  TTC_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  int s = TTC_OK;
+  cudaError_t e = cudaSuccess;
+  long long batched = 0;
+  for (auto& G : b->groups)
+    if (s == TTC_OK && G.g.tab_rows > 0) {
+      s = ttc_launch_omega_pass_batch(G.g, b->stream, 2);
+      ++batched;
+    }
+  if (b->prof) e = cudaEventRecordWithFlags(b->ev_beg, b->stream, cudaEventRecordExternal);
+  for (auto& G : b->groups)
+    if (s == TTC_OK && e == cudaSuccess) {
+      s = ttc_launch_omega_pass_batch(G.g, b->stream, 0);
+      ++batched;
+    }
+  if (b->prof && e == cudaSuccess) e = cudaEventRecordWithFlags(b->ev_end, b->stream, cudaEventRecordExternal);
+  for (auto& G : b->groups)
+    if (s == TTC_OK && e == cudaSuccess) {
+      s = ttc_launch_omega_pass_batch(G.g, b->stream, 1);
+      ++batched;
+    }
+  if (s == TTC_OK && e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
+  for (size_t i = 0; i < b->members.size() && s == TTC_OK && e == cudaSuccess; ++i) {
+    ttc_ctx* c = b->members[i];
+    bool own = c->stream != b->stream;
+    for (size_t j = 0; j < i && own; ++j)
+      if (b->members[j]->stream == c->stream) own = false;
+    cudaStream_t saved = c->stream;
+    if (!own) c->stream = b->stream;   // shared stream: run this member's branch in line
+    if (own) e = cudaStreamWaitEvent(c->stream, b->fork, 0);
+    if (e == cudaSuccess) s = ttc_launch_save_prev(c);
+    if (s == TTC_OK) s = ttc_launch_dense(c);
+    if (s == TTC_OK && own) {
+      e = cudaEventRecord(b->joins[i], c->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->joins[i], 0);
+    }
+    c->stream = saved;
+  }
+  cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  long long kernels = batched;
+  for (size_t i = 0; i < b->members.size(); ++i) {
+    kernels += b->members[i]->nlaunch - before[i];
+    b->members[i]->nlaunch = before[i];
+  }
+  if (s != TTC_OK || e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) ttc_record_cuda_error(e);
+    if (e2 != cudaSuccess) ttc_record_cuda_error(e2);
+    return s != TTC_OK ? s : TTC_ECUDA;
+  }
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    ttc_record_cuda_error(e);
+    return TTC_ECUDA;
+  }
+  b->kernels_per_step = kernels;
+  return TTC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ttc_batch_create(ttc_batch** out, ttc_ctx* const* members, int count, void* cuda_stream) {
+  if (!out || !members || count < 1) return TTC_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (!members[i] || !members[i]->have_obs || !members[i]->have_cores) return TTC_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (members[j] == members[i]) return TTC_EINVAL;
+  }
+  ttc_batch* b = new (std::nothrow) ttc_batch();
+  if (!b) return TTC_ENOMEM;
+  b->members.assign(members, members + count);
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    b->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    b->own_stream = (e == cudaSuccess);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  b->joins.assign(count, nullptr);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev_beg);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev_end);
+  if (e != cudaSuccess) {
+    ttc_record_cuda_error(e);
+    ttc_batch_destroy(b);
+    return TTC_ECUDA;
+  }
+  // members' pending work must be done before the batch reads their state
+  for (auto* c : b->members) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      ttc_record_cuda_error(e);
+      ttc_batch_destroy(b);
+      return TTC_ECUDA;
+    }
+  }
+  *out = b;
+  return TTC_OK;
+}
+
+int ttc_batch_step(ttc_batch* b) {
+  if (!b) return TTC_EINVAL;
+  bool stale = (b->exec == nullptr);
+  for (size_t i = 0; i < b->members.size() && !stale; ++i)
+    stale = (b->members[i]->cur_prec != b->prec_at_capture[i]);
+  if (stale) TTC_TRY(capture(b));
+  TTC_CUDA(cudaGraphLaunch(b->exec, b->stream));
+  b->nlaunch += b->kernels_per_step;
+  for (auto* c : b->members) ++c->iter;
+  if (b->prof) {
+    TTC_CUDA(cudaEventSynchronize(b->ev_end));
+    float t = 0.f;
+    TTC_CUDA(cudaEventElapsedTime(&t, b->ev_beg, b->ev_end));
+    b->prof_ms += t;
+    b->prof_count += 1;
+  }
+  return TTC_OK;
+}
+
+int ttc_batch_sync(ttc_batch* b) {
+  if (!b) return TTC_EINVAL;
+  TTC_CUDA(cudaStreamSynchronize(b->stream));
+  return TTC_OK;
+}
+
+int ttc_batch_profile_enable(ttc_batch* b, int on) {
+  if (!b) return TTC_EINVAL;
+  if ((on != 0) != b->prof) {
+    TTC_CUDA(cudaStreamSynchronize(b->stream));
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+  }
+  b->prof = on != 0;
+  return TTC_OK;
+}
+
+int ttc_batch_profile_read(ttc_batch* b, double* ms, int64_t* count, int reset) {
+  if (!b) return TTC_EINVAL;
+  if (ms) *ms = b->prof_ms;
+  if (count) *count = b->prof_count;
+  if (reset) {
+    b->prof_ms = 0.0;
+    b->prof_count = 0;
+  }
+  return TTC_OK;
+}
+
+int ttc_batch_launch_count(ttc_batch* b, int64_t* launches) {
+  if (!b || !launches) return TTC_EINVAL;
+  *launches = b->nlaunch;
+  return TTC_OK;
+}
+
+void ttc_batch_destroy(ttc_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  free_groups(b);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (auto ev : b->joins)
+    if (ev) cudaEventDestroy(ev);
+  if (b->ev_beg) cudaEventDestroy(b->ev_beg);
+  if (b->ev_end) cudaEventDestroy(b->ev_end);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+}  // extern "C"

@@ -43,6 +43,21 @@ struct DevProb {
   double* core64p[TTC_MAXM];
   double* prev64[TTC_MAXM];    // copy of T_l for the step-change metric
 
+  // interface tables: prefix L_j(x_0..x_{j-1}) = T_0(x_0)...T_{j-1}(x_{j-1})
+  // (a row of length r_j) and suffix R_j(x_j..x_{d-1}) = T_j(x_j)...T_{d-1}(x_{d-1})
+  // (a column of length r_j), for all index combinations, row-major mixed
+  // radix with the lowest mode most significant; row g at g * R (padded)
+  int ntab;
+  int tab_side[2 * TTC_MAXM];     // 0 prefix, 1 suffix
+  int tab_j[2 * TTC_MAXM];
+  long long tab_rows[2 * TTC_MAXM];
+  long long tab_row0[2 * TTC_MAXM];
+  long long tab_total;
+  int pre_tab[TTC_MAXM];          // mode k: table giving the prefix over modes < k (-1: none)
+  int suf_tab[TTC_MAXM];          // mode k: table giving the suffix over modes > k (-1: none)
+  float* tab32;
+  double* tab64;
+
   // Omega layout, per mode, in mode-k order
   const uint32_t* code[TTC_MAXM];
   const float* y32[TTC_MAXM];
@@ -132,6 +147,26 @@ __device__ __forceinline__ int pad_idx(const DevProb& P, int k, int a, int b) {
 
 __device__ __forceinline__ int code_coord(const DevProb& P, const uint32_t* words, int k) {
   return (int)((words[P.cword[k]] >> P.cshift[k]) & ((1u << P.cbits[k]) - 1u));
+}
+
+// the packed code of one entry, held in registers (selected without indexing)
+struct Code {
+  uint32_t w0, w1, w2, w3;
+  __device__ __forceinline__ uint32_t word(int i) const {
+    return i == 0 ? w0 : (i == 1 ? w1 : (i == 2 ? w2 : w3));
+  }
+};
+__device__ __forceinline__ Code load_code(const DevProb& P, int k, int e) {
+  Code c;
+  const uint32_t* p = P.code[k] + (long long)e * P.W;
+  c.w0 = __ldg(p);
+  c.w1 = P.W > 1 ? __ldg(p + 1) : 0u;
+  c.w2 = P.W > 2 ? __ldg(p + 2) : 0u;
+  c.w3 = P.W > 3 ? __ldg(p + 3) : 0u;
+  return c;
+}
+__device__ __forceinline__ int code_coord(const DevProb& P, const Code& c, int k) {
+  return (int)((c.word(P.cword[k]) >> P.cshift[k]) & ((1u << P.cbits[k]) - 1u));
 }
 
 // C (M x N, ldc) = alpha * op(A) * op(B) (+ beta * C when accumulate), on data

@@ -59,7 +59,23 @@ int ttc_upload_desc(ttc_ctx* c);
 // layout.cu
 int ttc_build_layout(ttc_ctx* c, const int32_t* idx_host, const double* y_host);
 
+// one group of a batch: members sharing the sampled-pass precision and rank
+// bucket, stepped by one launch of the batched sampled pass
+struct BatchGroup {
+  int prec;
+  int R;
+  int nprob;
+  const DevProb* probs;      // device array of the members' descriptors
+  const int* pass_base;      // device [nprob + 1]: block offsets of the sampled pass
+  const int* seg_base;       // device [nprob + 1]: block offsets of the slice reduction
+  const long long* tab_base; // device [nprob + 1]: row offsets of the interface tables
+  int pass_blocks, seg_blocks;
+  long long tab_rows;
+};
+
 // omega_pass.cu
+int ttc_launch_omega_pass_batch(const BatchGroup& g, cudaStream_t st, int phase);   // 0: pass, 1: slice reduction, 2: tables
+void ttc_plan_tables(ttc_ctx* c);
 int ttc_prepare_omega_pass();
 int ttc_launch_omega_pass(ttc_ctx* c, int prec);
 int ttc_launch_eval(ttc_ctx* c, const int32_t* idx_dev, long long M, int prec, double* out_dev);

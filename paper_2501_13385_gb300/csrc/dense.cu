@@ -89,7 +89,13 @@ __device__ __forceinline__ double ipow_2m(double y, int two_m) {
 }
 __device__ __forceinline__ double inv_root(double v, int m) {
   const int two_m = 2 * m;
-  double y = (double)powf((float)v, -1.0f / (float)two_m);
+  // seed: v^{-1/(2m)} = 2^{-(e + log2 f)/(2m)} with v = f 2^e, split into an
+  // integer power of two (exact) and an FP32 power of two in [1, 2)
+  int e;
+  const double f = frexp(v, &e);
+  const double t = -((double)e + (double)log2f((float)f)) / (double)two_m;
+  const double ti = floor(t);
+  double y = ldexp((double)exp2f((float)(t - ti)), (int)ti);
   const double c = 1.0 / (double)two_m;
   for (int it = 0; it < 2; ++it) y = y * fma(c, fma(-v, ipow_2m(y, two_m), 1.0), 1.0);
   return y;
@@ -169,9 +175,12 @@ __device__ void slice_contrib(const DevProb& P, const Stage& S, const Job& J, in
 // ---- small factorizations run by the last block ----------------------------
 
 // Lam[k]^{-1}, Gam[k]^{-1} (k = 1..d-1), then Q_k = Lam[k+1]^{-1} H_k Gam[k+1]^{-1};
-// one warp per matrix.
+// one warp per matrix (FP32 Cholesky + FP64 Newton-Schulz); matrices whose
+// residual stays above 1e-12 are redone by the block in FP64.
 __device__ void post_small_proj(const DevProb& P, double* sm) {
   const int m = P.m, warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+  __shared__ int redo[2 * TTC_MAXM];
+  __shared__ int flag;
   int rmax = 1;
   for (int k = 0; k <= m; ++k) rmax = max(rmax, P.r[k]);
   const int nn = rmax * rmax;
@@ -179,13 +188,14 @@ __device__ void post_small_proj(const DevProb& P, double* sm) {
   double* T = sm + warp * 2 * nn;
   float* Lf = reinterpret_cast<float*>(sm + nw * 2 * nn) + warp * 2 * nn;
   float* Lif = Lf + nn;
-  int bad = 0;
+  if (threadIdx.x == 0) flag = 0;
   for (int j = warp; j < 2 * (m - 1); j += nw) {
     const int k = 1 + (j >> 1);
     const int r = P.r[k];
     const double* A = P.small + ((j & 1) ? P.off_gam[k] : P.off_lam[k]);
     double* X = P.small + ((j & 1) ? P.off_gami[k] : P.off_lami[k]);
-    bad |= warp_spd_inverse(A, r, r, X, r, Lf, Lif, T);
+    double res = warp_spd_inverse(A, r, r, X, r, Lf, Lif, T);
+    if (lane == 0) redo[j] = !(res < 1e-12);
   }
   if (threadIdx.x == 0) {
     P.small[P.off_lami[0]] = 1.0 / P.small[P.off_lam[0]];
@@ -193,6 +203,21 @@ __device__ void post_small_proj(const DevProb& P, double* sm) {
   }
   __threadfence_block();
   __syncthreads();
+  for (int j = 0; j < 2 * (m - 1); ++j) {          // FP64 fallback, whole block
+    if (!redo[j]) continue;
+    const int k = 1 + (j >> 1);
+    const int r = P.r[k];
+    const double* A = P.small + ((j & 1) ? P.off_gam[k] : P.off_lam[k]);
+    double* X = P.small + ((j & 1) ? P.off_gami[k] : P.off_lami[k]);
+    double* Ac = sm;
+    double* work = sm + r * r;
+    for (int i = threadIdx.x; i < r * r; i += blockDim.x) Ac[i] = A[i];
+    __syncthreads();
+    blk_spd_inverse(Ac, r, work, &flag);
+    for (int i = threadIdx.x; i < r * r; i += blockDim.x) X[i] = Ac[i];
+    __threadfence_block();
+    __syncthreads();
+  }
   for (int k = warp; k + 1 < m; k += nw) {
     const int r = P.r[k + 1];
     warp_gemm<double>(r, r, r, P.small + P.off_lami[k + 1], r, false, P.small + P.off_h[k], r, false, T, r, 1.0,
@@ -200,23 +225,83 @@ __device__ void post_small_proj(const DevProb& P, double* sm) {
     warp_gemm<double>(r, r, r, T, r, false, P.small + P.off_gami[k + 1], r, false, P.small + P.off_qm[k], r, 1.0,
                       false);
   }
-  unsigned any = __ballot_sync(0xffffffffu, bad);
-  if (lane == 0 && any) atomicOr(P.flags, 2u);
+  __syncthreads();
+  if (threadIdx.x == 0 && flag) atomicOr(P.flags, 2u);
+}
+
+// Orthonormal basis U of span(W) (q x r): FP32 CholeskyQR, repeated once if
+// needed, accepted when ||Z^T Z - I||_max < 1e-4 and then polished in FP64 by
+// Z (I - E/2 + 3E^2/8) (error O(E^3)); an FP64 Cholesky when the FP32 passes
+// cannot reach that (ill-conditioned W).  Scratch s: 2 q*r + 5 r*r doubles.
+__device__ void orthonormalize(const double* W, int q, int r, double* U, double* s, double* red, float* Lf,
+                               float* Lif, int* bad) {
+  const int tid = threadIdx.x;
+  double* Z = s;
+  double* Z2 = Z + q * r;
+  double* G = Z2 + q * r;
+  double* E = G + r * r;
+  double* F = E + r * r;
+  double* Li = F + r * r;
+  double* work = Li + r * r;
+  const double* src = W;
+  for (int pass = 0; pass < 2; ++pass) {
+    blk_gemm<double>(r, r, q, src, r, true, src, r, false, G, r, 1.0, false);   // G = src^T src
+    __syncthreads();
+    if (tid < 32) warp_chol_inv32(G, r, r, Lf, Lif);
+    __syncthreads();
+    double* dst = (pass == 0) ? Z : Z2;
+    for (int i = tid; i < q * r; i += blockDim.x) {                               // dst = src L^{-T}
+      int a = i / r, c = i - (i / r) * r;
+      double acc = 0.0;
+      for (int t = 0; t <= c; ++t) acc = fma(src[a * r + t], (double)Lif[c * r + t], acc);
+      dst[i] = acc;
+    }
+    __syncthreads();
+    blk_gemm<double>(r, r, q, dst, r, true, dst, r, false, E, r, 1.0, false);   // E = dst^T dst - I
+    __syncthreads();
+    double em = 0.0;
+    for (int i = tid; i < r * r; i += blockDim.x) {
+      double v = E[i] - (((i / r) == (i % r)) ? 1.0 : 0.0);
+      E[i] = v;
+      em = fmax(em, fabs(v));
+    }
+    em = blk_max(em, red);
+    if (em < 1e-4) {   // polish: F = I - E/2 + 3/8 E^2, U = dst F
+      blk_gemm<double>(r, r, r, E, r, false, E, r, false, F, r, 0.375, false);
+      __syncthreads();
+      for (int i = tid; i < r * r; i += blockDim.x) F[i] += (((i / r) == (i % r)) ? 1.0 : 0.0) - 0.5 * E[i];
+      __syncthreads();
+      blk_gemm<double>(q, r, r, dst, r, false, F, r, false, U, r, 1.0, false);
+      __syncthreads();
+      return;
+    }
+    src = dst;
+  }
+  // FP64 Cholesky of W^T W
+  blk_gemm<double>(r, r, q, W, r, true, W, r, false, G, r, 1.0, false);
+  __syncthreads();
+  blk_chol_linv64(G, r, r, Li, work, bad);
+  for (int i = tid; i < q * r; i += blockDim.x) {
+    int a = i / r, c = i - (i / r) * r;
+    double acc = 0.0;
+    for (int t = 0; t <= c; ++t) acc = fma(W[a * r + t], Li[c * r + t], acc);
+    U[i] = acc;
+  }
+  __syncthreads();
 }
 
 // Bond k of the retraction: from N_k (in P.small) and Psi[k+1], P_k and S_k.
 __device__ void post_bond(const DevProb& P, int k, double* sm) {
   const int q = P.q[k + 1], r = P.r[k + 1];
   const int tid = threadIdx.x;
-  double* N = sm;                 // q x q
-  double* A = N + q * q;          // q x q : Psi N
-  double* U = A + q * q;          // q x r
-  double* W = U + q * r;          // q x r
-  double* Z = W + q * r;          // q x r
-  double* G = Z + q * r;          // r x r
-  double* Bm = G + r * r;         // r x r
-  double* Rinv = Bm + r * r;      // r x r
-  double* red = Rinv + r * r;     // blockDim
+  double* N = sm;                  // q x q
+  double* A = N + q * q;           // q x q : Psi N
+  double* U = A + q * q;           // q x r
+  double* W = U + q * r;           // q x r
+  double* V = W + q * r;           // q x r
+  double* Bm = V + q * r;          // r x r
+  double* scr = Bm + r * r;        // 2 q r + 5 r r
+  double* red = scr + 2 * q * r + 5 * r * r;   // blockDim
   float* Lf = reinterpret_cast<float*>(red + blockDim.x);
   float* Lif = Lf + r * r;
   __shared__ int bad;
@@ -234,79 +319,73 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
   for (; it < kMaxIter; ++it) {
     blk_gemm<double>(q, r, q, A, q, false, U, r, false, W, r, 1.0, false);       // W = A U
     __syncthreads();
-    blk_gemm<double>(r, r, q, W, r, true, W, r, false, G, r, 1.0, false);        // G = W^T W
-    __syncthreads();
-    if (tid < 32) {
-      int b = warp_chol_inv32(G, r, r, Lf, Lif);
-      if (tid == 0 && b) bad = 1;
-    }
-    __syncthreads();
-    for (int i = tid; i < q * r; i += blockDim.x) {                               // Z = W L^{-T}
-      int a = i / r, c = i - (i / r) * r;
-      double acc = 0.0;
-      for (int t = 0; t <= c; ++t) acc = fma(W[a * r + t], (double)Lif[c * r + t], acc);
-      Z[i] = acc;
-    }
-    __syncthreads();
-    // FP64 orthonormality: E = Z^T Z - I, Z <- Z (I - E/2 + 3E^2/8)
-    blk_gemm<double>(r, r, q, Z, r, true, Z, r, false, Bm, r, 1.0, false);       // Bm = Z^T Z
-    __syncthreads();
-    for (int i = tid; i < r * r; i += blockDim.x) Bm[i] -= ((i / r) == (i % r)) ? 1.0 : 0.0;
-    __syncthreads();
-    blk_gemm<double>(r, r, r, Bm, r, false, Bm, r, false, Rinv, r, 0.375, false); // 3/8 E^2
-    __syncthreads();
-    for (int i = tid; i < r * r; i += blockDim.x) Rinv[i] += (((i / r) == (i % r)) ? 1.0 : 0.0) - 0.5 * Bm[i];
-    __syncthreads();
-    blk_gemm<double>(q, r, r, Z, r, false, Rinv, r, false, W, r, 1.0, false);    // W = Z F (orthonormal)
-    __syncthreads();
-    blk_gemm<double>(r, r, q, U, r, true, W, r, false, Bm, r, 1.0, false);       // Bm = U^T W
+    orthonormalize(W, q, r, V, scr, red, Lf, Lif, &bad);                         // V = orth(W)
+    blk_gemm<double>(r, r, q, U, r, true, V, r, false, Bm, r, 1.0, false);       // Bm = U^T V
     __syncthreads();
     double dd = 0.0;
-    for (int i = tid; i < q * r; i += blockDim.x) {                               // movement W - U Bm
+    for (int i = tid; i < q * r; i += blockDim.x) {                               // movement V - U Bm
       int a = i / r, c = i - (i / r) * r;
-      double acc = W[i];
+      double acc = V[i];
       for (int t = 0; t < r; ++t) acc = fma(-U[a * r + t], Bm[t * r + c], acc);
       dd = fma(acc, acc, dd);
     }
     double mv = blk_sum(dd, red);
-    for (int i = tid; i < q * r; i += blockDim.x) U[i] = W[i];
+    for (int i = tid; i < q * r; i += blockDim.x) U[i] = V[i];
     __syncthreads();
     if (mv <= kMoveTol2 * r) {
       ++it;
       break;
     }
   }
-  // normalisation: R^T R = U^T N U, R^{-1} from FP32 Cholesky plus a
-  // second-order FP64 correction (E = R0^{-T} G R0^{-1} - I,
-  // R^{-1} = R0^{-1} (I - E/2 + 3E^2/8))
+  // normalisation: T_k = C' U R^{-1} with R^T R = G = U^T N U; R^{-1} from the
+  // FP32 Cholesky of G checked by E = R^{-T} G R^{-1} - I (FP64 Cholesky when
+  // ||E|| >= 1e-4), then polished: R^{-1} (I - E/2 + 3E^2/8)
+  double* G = scr;
+  double* Li = scr + r * r;
+  double* work = Li + r * r;
+  double* E = work + r * r;
+  double* F = E + r * r;
   blk_gemm<double>(q, r, q, N, q, false, U, r, false, W, r, 1.0, false);         // W = N U
   __syncthreads();
   blk_gemm<double>(r, r, q, U, r, true, W, r, false, G, r, 1.0, false);          // G = U^T N U
   __syncthreads();
-  if (tid < 32) {
-    int b = warp_chol_inv32(G, r, r, Lf, Lif);
-    if (tid == 0 && b) bad = 1;
-  }
+  if (tid < 32) warp_chol_inv32(G, r, r, Lf, Lif);
   __syncthreads();
+  double* Rinv = Bm;
   for (int i = tid; i < r * r; i += blockDim.x) {                                 // Rinv = L^{-T}
     int a = i / r, c = i - (i / r) * r;
     Rinv[i] = (double)Lif[c * r + a];
   }
   __syncthreads();
-  blk_gemm<double>(r, r, r, G, r, false, Rinv, r, false, Bm, r, 1.0, false);     // Bm = G Rinv
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    blk_gemm<double>(r, r, r, G, r, false, Rinv, r, false, F, r, 1.0, false);    // F = G Rinv
+    __syncthreads();
+    blk_gemm<double>(r, r, r, Rinv, r, true, F, r, false, E, r, 1.0, false);     // E = Rinv^T G Rinv
+    __syncthreads();
+    double em = 0.0;
+    for (int i = tid; i < r * r; i += blockDim.x) {
+      double v = E[i] - (((i / r) == (i % r)) ? 1.0 : 0.0);
+      E[i] = v;
+      em = fmax(em, fabs(v));
+    }
+    em = blk_max(em, red);
+    if (em < 1e-4) break;
+    // FP64 Cholesky instead
+    blk_chol_linv64(G, r, r, Li, work, &bad);
+    for (int i = tid; i < r * r; i += blockDim.x) {
+      int a = i / r, c = i - (i / r) * r;
+      Rinv[i] = Li[c * r + a];
+    }
+    __syncthreads();
+  }
+  blk_gemm<double>(r, r, r, E, r, false, E, r, false, F, r, 0.375, false);       // F = 3/8 E^2
   __syncthreads();
-  blk_gemm<double>(r, r, r, Rinv, r, true, Bm, r, false, Z, r, 1.0, false);      // Z = E + I
+  for (int i = tid; i < r * r; i += blockDim.x) F[i] += (((i / r) == (i % r)) ? 1.0 : 0.0) - 0.5 * E[i];
   __syncthreads();
-  for (int i = tid; i < r * r; i += blockDim.x) Z[i] -= ((i / r) == (i % r)) ? 1.0 : 0.0;   // E
-  __syncthreads();
-  blk_gemm<double>(r, r, r, Z, r, false, Z, r, false, Bm, r, 0.375, false);      // Bm = 3/8 E^2
-  __syncthreads();
-  for (int i = tid; i < r * r; i += blockDim.x) Bm[i] += (((i / r) == (i % r)) ? 1.0 : 0.0) - 0.5 * Z[i];   // F
-  __syncthreads();
-  blk_gemm<double>(r, r, r, Rinv, r, false, Bm, r, false, G, r, 1.0, false);     // G = Rinv F
+  blk_gemm<double>(r, r, r, Rinv, r, false, F, r, false, work, r, 1.0, false);   // Rinv F
   __syncthreads();
   double* Pk = P.small + P.off_pk[k];
-  blk_gemm<double>(q, r, r, U, r, false, G, r, false, Pk, r, 1.0, false);        // P = U R^{-1}
+  blk_gemm<double>(q, r, r, U, r, false, work, r, false, Pk, r, 1.0, false);     // P = U R^{-1}
   __threadfence_block();
   __syncthreads();
   blk_gemm<double>(r, q, q, Pk, r, true, N, q, false, P.small + P.off_sk[k], q, 1.0, false);   // S = P^T N
@@ -739,7 +818,7 @@ int ttc_alloc_dense(ttc_ctx* c) {
   size_t red_need = sizeof(double) * (size_t)(2 * qmax * qmax);
   red_need = std::max(red_need, sizeof(double) * (size_t)(2 * TTC_MAXR * TTC_MAXR));
   size_t proj_need = sizeof(double) * (size_t)(8 * 2 * rmax * rmax) + sizeof(float) * (size_t)(8 * 2 * rmax * rmax);
-  size_t bond_need = sizeof(double) * (size_t)(2 * qmax * qmax + 3 * qmax * rmax + 3 * rmax * rmax + kThreads) +
+  size_t bond_need = sizeof(double) * (size_t)(2 * qmax * qmax + 5 * qmax * rmax + 6 * rmax * rmax + kThreads) +
                      sizeof(float) * (size_t)(2 * rmax * rmax);
   pl.smem_stage = std::max(red_need, std::max(proj_need, bond_need)) + 64;
   TTC_CUDA(cudaFuncSetAttribute(k_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem_stage));

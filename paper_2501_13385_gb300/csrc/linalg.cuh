@@ -242,11 +242,12 @@ __device__ void warp_gemm(int M, int N, int K, const T* A, int lda, bool ta, con
 }
 
 // One warp: X = A^{-1} for SPD A (n <= 32), FP64 result.  X0 = L^{-T} L^{-1}
-// from the FP32 Cholesky, then two Newton-Schulz steps X <- X + X (I - A X)
-// in FP64 (each squares the relative error: 1e-7 kappa -> FP64 rounding).
-// Scratch: L, Li (n*n floats each), T (2*n*n doubles).  Returns the pivot flag.
-static __device__ int warp_spd_inverse(const double* A, int lda, int n, double* X, int ldx, float* L, float* Li,
-                                       double* T) {
+// from the FP32 Cholesky, then Newton-Schulz steps X <- X + X (I - A X) in
+// FP64 (each squares the relative error).  Returns max |I - A X| after the
+// last step, or a huge value if the pivots failed, so the caller can fall
+// back to the FP64 factorization.  Scratch: L, Li (n*n floats), T (2 n*n doubles).
+static __device__ double warp_spd_inverse(const double* A, int lda, int n, double* X, int ldx, float* L, float* Li,
+                                          double* T) {
   const int lane = threadIdx.x & 31;
   int bad = warp_chol_inv32(A, lda, n, L, Li);
   for (int idx = lane; idx < n * n; idx += 32) {
@@ -259,10 +260,16 @@ static __device__ int warp_spd_inverse(const double* A, int lda, int n, double* 
   __syncwarp();
   double* T1 = T;
   double* T2 = T + n * n;
-  for (int it = 0; it < 2; ++it) {
+  double res = 0.0;
+  for (int it = 0; it < 4; ++it) {
     warp_gemm<double>(n, n, n, A, lda, false, X, ldx, false, T1, n, -1.0, false);   // T1 = -A X
     for (int i = lane; i < n; i += 32) T1[i * n + i] += 1.0;                          // T1 = I - A X
     __syncwarp();
+    res = 0.0;
+    for (int idx = lane; idx < n * n; idx += 32) res = fmax(res, fabs(T1[idx]));
+    for (int o = 16; o > 0; o >>= 1) res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
+    if (!(res < 1.0)) break;                   // no contraction: leave it to the FP64 path
+    if (it >= 2 && res < 1e-13) break;         // converged
     warp_gemm<double>(n, n, n, X, ldx, false, T1, n, false, T2, n, 1.0, false);      // T2 = X T1
     for (int idx = lane; idx < n * n; idx += 32) {
       int i = idx / n, j = idx - (idx / n) * n;
@@ -270,5 +277,62 @@ static __device__ int warp_spd_inverse(const double* A, int lda, int n, double* 
     }
     __syncwarp();
   }
-  return bad;
+  return (bad || !(res < 1.0)) ? 1e300 : res;
+}
+
+// Deterministic block-wide maximum of one double per thread.
+static __device__ double blk_max(double v, double* sh) {
+  __syncthreads();
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  double out = sh[0];
+  __syncthreads();
+  return out;
+}
+
+// FP64 lower Cholesky factor of SPD G (n x n, ldg) and Li = L^{-1} (n x n,
+// row-major), block-parallel (the slow but robust path, for matrices whose
+// conditioning defeats the FP32 factorization).  `work` holds n*n doubles.
+// A pivot that is not positive is replaced by a tiny value (flag set).
+static __device__ void blk_chol_linv64(const double* G, int ldg, int n, double* Li, double* work, int* flag) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int i = tid; i < n * n; i += bd) work[i] = G[(i / n) * ldg + (i % n)];
+  __syncthreads();
+  double scale = 0.0;
+  for (int i = 0; i < n; ++i) scale = fmax(scale, fabs(work[i * n + i]));
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      double d = work[j * n + j];
+      double floor_ = 1e-300 * (scale > 0 ? scale : 1.0) + 1e-300;
+      if (!(d > floor_)) {
+        d = floor_;
+        *flag = 1;
+      }
+      work[j * n + j] = sqrt(d);
+    }
+    __syncthreads();
+    const double piv = work[j * n + j];
+    for (int i = j + 1 + tid; i < n; i += bd) work[i * n + j] /= piv;
+    __syncthreads();
+    const int t = n - j - 1;
+    for (int idx = tid; idx < t * t; idx += bd) {
+      int i = j + 1 + idx / t, k = j + 1 + idx % t;
+      if (k <= i) work[i * n + k] -= work[i * n + j] * work[k * n + j];
+    }
+    __syncthreads();
+  }
+  for (int c = tid; c < n; c += bd) {
+    for (int i = 0; i < c; ++i) Li[i * n + c] = 0.0;
+    Li[c * n + c] = 1.0 / work[c * n + c];
+    for (int i = c + 1; i < n; ++i) {
+      double acc = 0.0;
+      for (int k = c; k < i; ++k) acc = fma(work[i * n + k], Li[k * n + c], acc);
+      Li[i * n + c] = -acc / work[i * n + i];
+    }
+  }
+  __syncthreads();
 }

@@ -59,7 +59,8 @@ EXPORTS = [
     "ttc_set_truth", "ttc_step", "ttc_solve", "ttc_relerr", "ttc_eval", "ttc_get_residual",
     "ttc_get_slice_energy", "ttc_get_scatter", "ttc_get_layout", "ttc_profile_enable", "ttc_profile_read",
     "ttc_device_bytes", "ttc_destroy", "ttc_strerror", "ttc_last_cuda_error", "ttc_launch_count",
-    "ttc_tt_dist2_static",
+    "ttc_tt_dist2_static", "ttc_batch_create", "ttc_batch_step", "ttc_batch_sync", "ttc_batch_profile_enable",
+    "ttc_batch_profile_read", "ttc_batch_launch_count", "ttc_batch_destroy",
 ]
 
 
@@ -95,6 +96,13 @@ def lib():
         "ttc_launch_count": (C.c_int, [vp, i64p]),
         "ttc_tt_dist2_static": (C.c_int, [C.c_int, i64p, i32p, C.POINTER(vp), i32p, C.POINTER(vp), vp, vp]),
         "ttc_destroy": (None, [vp]),
+        "ttc_batch_create": (C.c_int, [C.POINTER(vp), C.POINTER(vp), C.c_int, vp]),
+        "ttc_batch_step": (C.c_int, [vp]),
+        "ttc_batch_sync": (C.c_int, [vp]),
+        "ttc_batch_profile_enable": (C.c_int, [vp, C.c_int]),
+        "ttc_batch_profile_read": (C.c_int, [vp, dp, i64p, C.c_int]),
+        "ttc_batch_launch_count": (C.c_int, [vp, i64p]),
+        "ttc_batch_destroy": (None, [vp]),
         "ttc_strerror": (C.c_char_p, [C.c_int]),
         "ttc_last_cuda_error": (C.c_char_p, []),
     }
@@ -278,3 +286,53 @@ class Context:
         v = C.c_int64()
         _check(lib().ttc_device_bytes(self._h, C.byref(v)), "ttc_device_bytes")
         return v.value
+
+
+class Batch:
+    """Several contexts stepped together by one CUDA graph launch per iteration
+    (ttc_batch_*).  Holds references to its members; close it before them."""
+
+    def __init__(self, members: Sequence[Context], stream: Optional[int] = None):
+        self.members = list(members)
+        arr = (C.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        self._h = C.c_void_p()
+        _check(lib().ttc_batch_create(C.byref(self._h), arr, len(self.members),
+                                      C.c_void_p(stream) if stream else None), "ttc_batch_create")
+
+    def step(self):
+        _check(lib().ttc_batch_step(self._h), "ttc_batch_step")
+
+    def sync(self):
+        _check(lib().ttc_batch_sync(self._h), "ttc_batch_sync")
+
+    def profile_enable(self, on: bool = True):
+        _check(lib().ttc_batch_profile_enable(self._h, 1 if on else 0), "ttc_batch_profile_enable")
+
+    def profile_read(self, reset: bool = False):
+        ms = C.c_double()
+        cnt = C.c_int64()
+        _check(lib().ttc_batch_profile_read(self._h, C.byref(ms), C.byref(cnt), 1 if reset else 0),
+               "ttc_batch_profile_read")
+        return ms.value, cnt.value
+
+    def launch_count(self) -> int:
+        v = C.c_int64()
+        _check(lib().ttc_batch_launch_count(self._h, C.byref(v)), "ttc_batch_launch_count")
+        return v.value
+
+    def close(self):
+        if self._h:
+            lib().ttc_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

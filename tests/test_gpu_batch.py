@@ -1,0 +1,83 @@
+"""Batches: one graph launch steps many independent problems.  Each member
+must compute exactly what it computes when stepped alone (bitwise), across
+different orders, mode sizes, ranks (rank buckets) and precisions.  GPU only."""
+import numpy as np
+import pytest
+
+from paper_2501_13385_gb300 import ttc
+from paper_2501_13385_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2501_13385_gb300 import build
+    build.build()
+    ttc.lib()
+
+
+MEMBERS = [
+    (dict(n=[10, 10, 10, 10], r=[1, 2, 2, 2, 1], count=3000), ttc.PREC_FP64),
+    (dict(n=[30, 20, 25], r=[1, 4, 3, 1], count=3000), ttc.PREC_FP32),
+    (dict(n=[60, 8], r=[1, 2, 1], count=400), ttc.PREC_FP32),
+    (dict(n=[6, 300, 5], r=[1, 3, 3, 1], count=8000), ttc.PREC_FP32),   # a mode > 256
+    (dict(n=[4, 4, 4, 4, 4, 4], r=[1, 4, 6, 8, 6, 4, 1], count=2500), ttc.PREC_FP64),
+    (dict(n=[30, 28, 26], r=[1, 9, 10, 1], count=15000), ttc.PREC_FP32),  # rank bucket 16
+]
+
+
+def make(spec, prec, seed):
+    P = w.random_problem(seed, spec["n"], spec["r"], spec["count"], init_rel=0.05)
+    c = ttc.Context(P.n, P.r, precision=prec)
+    c.set_observations(P.idx, P.y)
+    c.set_cores(P.init)
+    return P, c
+
+
+def test_batch_members_bitwise_equal_to_alone():
+    steps = 4
+    alone = []
+    for i, (spec, prec) in enumerate(MEMBERS):
+        P, c = make(spec, prec, 100 + i)
+        for _ in range(steps):
+            c.step()
+        alone.append(c.get_cores())
+        c.close()
+    ctxs = [make(spec, prec, 100 + i)[1] for i, (spec, prec) in enumerate(MEMBERS)]
+    with ttc.Batch(ctxs) as b:
+        for _ in range(steps):
+            b.step()
+        b.sync()
+        assert b.launch_count() > 0
+    for c, ref in zip(ctxs, alone):
+        got = c.get_cores()
+        for a, r in zip(got, ref):
+            assert np.array_equal(a, r)
+        c.close()
+
+
+def test_batch_profile_and_member_reuse():
+    specs = [MEMBERS[1], MEMBERS[3]]
+    ctxs = [make(spec, prec, 200 + i)[1] for i, (spec, prec) in enumerate(specs)]
+    with ttc.Batch(ctxs) as b:
+        b.profile_enable(True)
+        for _ in range(3):
+            b.step()
+        ms, cnt = b.profile_read()
+        assert cnt == 3 and ms > 0
+    # members remain usable on their own after the batch is gone
+    for c in ctxs:
+        c.step()
+        c.close()
+
+
+def test_batch_rejects_bad_members():
+    P, c = make(MEMBERS[1][0], ttc.PREC_FP32, 7)
+    with pytest.raises(ttc.TTCError):
+        ttc.Batch([c, c])
+    empty = ttc.Context([5, 6, 7], [1, 2, 2, 1])
+    with pytest.raises(ttc.TTCError):
+        ttc.Batch([c, empty])
+    empty.close()
+    c.close()

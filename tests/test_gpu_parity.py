@@ -37,6 +37,8 @@ SHAPES = [
     ([6, 300, 5], [1, 5, 5, 1], 4000),        # a mode > 256 needs two radix digits
     ([4, 4, 4, 4, 4, 4], [1, 4, 6, 8, 6, 4, 1], 2500),
     ([9, 8, 7], [1, 1, 2, 1], 200),           # rank-1 bond
+    ([30, 28, 26], [1, 9, 10, 1], 15000),     # rank bucket 16 (shared-memory outer products)
+    ([40, 40, 40], [1, 20, 20, 1], 48000),    # rank bucket 32
 ]
 
 

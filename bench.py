@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-solves", type=int, default=3)
     ap.add_argument("--e2e-iters", type=int, default=20)
+    ap.add_argument("--serve-requests", type=int, default=64,
+                    help="requests streamed through the serving engine (0: skip)")
     ap.add_argument("--batch", type=int, default=32,
                     help="independent problems per step (one CUDA graph launch); 1 = a single problem")
     return ap.parse_args()
@@ -206,6 +208,7 @@ def ttc_arm(args):
 
     from paper_2501_13385_gb300 import build, ttc
     from paper_2501_13385_gb300 import workloads as w
+    from paper_2501_13385_gb300.replicas import max_over_ranks, replica_seeds, whole_job_rate
 
     if world > 1:
         dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -214,7 +217,7 @@ def ttc_arm(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     B = max(1, args.batch)
-    probs = [w.orthogonal_cubic(rank * B + i) for i in range(B)]
+    probs = [w.orthogonal_cubic(s) for s in replica_seeds(rank, B)]
     N = probs[0].N
 
     def make_ctx(P, prec, stop=ttc.STOP_NONE, **kw):
@@ -262,12 +265,9 @@ def ttc_arm(args):
     batch.close()
     for c in ctxs:
         c.close()
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world)
     ms_per_step = total_ms / K
-    value = world * B * N * K / (total_ms / 1e3)
+    value = whole_job_rate(world, B, N, K, total_ms)
 
     # iterations and time to rel.err <= 1e-6 (vs T*) for one problem, mixed and plain FP64
     P = probs[0]
@@ -316,7 +316,36 @@ def ttc_arm(args):
     for c in ectx:
         c.close()
     h2d = sum(a.nbytes for a in idx_h) + sum(a.nbytes for a in y_h) + sum(a.nbytes for cs in init_h for a in cs)
-    e2e_val = world * B * N * args.e2e_iters / (statistics.mean(e2e_ms) / 1e3)
+    e2e_step_ms = max_over_ranks(statistics.mean(e2e_ms), world)
+    e2e_val = whole_job_rate(world, B, N, args.e2e_iters, e2e_step_ms)
+
+    # serving: a burst of solve requests (rel.err <= 1e-6 against T*, mixed
+    # precision) through the continuous-batching engine with B slots
+    serving = None
+    if args.serve_requests > 0:
+        sprobs = [probs[i] if i < B else w.orthogonal_cubic(rank * 100000 + 50000 + i)
+                  for i in range(args.serve_requests)]
+        sopt = ttc.default_options(precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_RELERR, tol=1e-6, max_iter=200)
+        with ttc.Server(max_slots=B) as srv:
+            # one request first so that kernel set-up is outside the measurement
+            srv.poll(srv.submit(P.n, P.r, P.idx, P.y, P.init, truth=P.truth, options=sopt), cores=False)
+            s0 = srv.stats()
+            t0 = time.perf_counter()
+            tickets = [srv.submit(Q.n, Q.r, Q.idx, Q.y, Q.init, truth=Q.truth, options=sopt) for Q in sprobs]
+            res = [srv.poll(t) for t in tickets]
+            wall = time.perf_counter() - t0
+            s1 = srv.stats()
+        lat = sorted(r["latency_ms"] for r in res)
+        pct = lambda q: lat[min(len(lat) - 1, max(0, int(np.ceil(q * len(lat))) - 1))]
+        serving = {
+            "requests": len(res), "max_slots": B, "stop": "rel.err <= 1e-6 vs T*, mixed precision",
+            "converged": sum(1 for r in res if r["converged"]),
+            "requests_per_s": len(res) / wall, "wall_ms": 1e3 * wall,
+            "latency_p50_ms": pct(0.50), "latency_p99_ms": pct(0.99),
+            "mean_iters": float(np.mean([r["iters"] for r in res])),
+            "entry_iters_per_s": (s1["entry_iterations"] - s0["entry_iterations"]) / wall,
+            "gpu_launches": s1["launches"] - s0["launches"],
+        }
 
     # roofline of the dominant kernel: the batched sampled pass, one launch per step
     peaks = {}
@@ -357,8 +386,9 @@ def ttc_arm(args):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "Ω-entries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": out_bytes, "iters_per_step": args.e2e_iters,
-                    "ms_per_step": statistics.mean(e2e_ms)},
+                    "ms_per_step": e2e_step_ms},
             "gpu_launches": launches,
+            "serving": serving,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

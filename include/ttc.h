@@ -61,7 +61,8 @@ enum {
 enum {
   TTC_STOP_RELERR = 0, /* ||T_l - T*||_F / ||T*||_F <= tol (needs ttc_set_truth) */
   TTC_STOP_STEP = 1,   /* ||T_{l+1} - T_l||_F <= tol * max(1, ||T_l||_F) (Section 5, noise experiment) */
-  TTC_STOP_NONE = 2    /* run exactly max_iter iterations */
+  TTC_STOP_NONE = 2,   /* run exactly max_iter iterations */
+  TTC_STOP_RESID = 3   /* ||P_Omega(T_l) - y|| <= tol ||y|| (residual on Omega; no extra kernels) */
 };
 
 typedef struct {
@@ -203,6 +204,92 @@ int ttc_batch_profile_read(ttc_batch* b, double* ms, int64_t* count, int reset);
 /* Kernels launched by the batch so far (all graph kernel nodes of each step). */
 int ttc_batch_launch_count(ttc_batch* b, int64_t* launches);
 void ttc_batch_destroy(ttc_batch* b);
+
+/* Serving: continuous batching of completion requests.
+ *
+ * A server owns an engine thread that runs requests on the current device.
+ * ttc_submit copies a request (shape, Omega, y, starting cores, optional
+ * truth and options) into host memory and queues it; the engine admits queued
+ * requests in submission order while their device memory fits the budget and
+ * fewer than max_slots are active, steps every active request together (one
+ * batched iteration per tick, as ttc_batch_step), applies each request's stop
+ * rule after every iteration (as ttc_solve: the precision switch of
+ * TTC_PREC_MIXED, the check interval, max_iter), and retires finished
+ * requests, copying their cores to host memory and freeing their device
+ * memory, while the others keep running.  A request's iterates do not depend
+ * on which other requests share its ticks: it computes exactly what ttc_solve
+ * computes for it alone.  The paper solves one problem at a time; the
+ * server is the batching layer around its Algorithm 2.
+ *
+ * device_mem_budget: bytes of device memory the active requests may hold
+ * (0: 80% of the free memory at creation).  A request whose estimate
+ * exceeds the budget is rejected by ttc_submit with TTC_ENOMEM.
+ * cuda_stream: stream of the batched work (NULL: the server creates one).
+ * Errors: TTC_EINVAL (null pointer, max_slots < 1), TTC_ECUDA. */
+typedef struct ttc_server ttc_server;
+int ttc_server_create(ttc_server** out, size_t device_mem_budget, int max_slots, void* cuda_stream);
+
+/* One request.  All pointers are host pointers, read only during
+ * ttc_submit (the server keeps copies).  n[d], r[d+1] and idx[N*d] (row-major
+ * multi-indices) as in ttc_create / ttc_set_observations; init[k] the
+ * starting cores; truth_r / truth (both NULL, or both set) the reference
+ * train for TTC_STOP_RELERR; opt NULL: defaults with TTC_STOP_RESID. */
+typedef struct {
+  int d;
+  const int64_t* n;
+  const int32_t* r;
+  int64_t N;
+  const int32_t* idx;
+  const double* y;
+  const double* const* init;
+  const int32_t* truth_r;
+  const double* const* truth;
+  const ttc_options* opt;
+} ttc_request;
+
+/* Queue a request; *ticket identifies it in ttc_poll.  Errors: TTC_EINVAL
+ * (null pointers, bad shape), TTC_EUNSUPPORTED (limits of ttc_create),
+ * TTC_ENOMEM (estimate above the budget), TTC_EBUSY (server shutting down).
+ * Errors of the data itself (TTC_ERANGE, TTC_EDUP, TTC_ENONFINITE) are found at
+ * admission and returned in the request's result. */
+int ttc_submit(ttc_server* s, const ttc_request* req, uint64_t* ticket);
+
+typedef struct {
+  int status;          /* TTC_OK, TTC_ENOTCONV or the error that ended the request */
+  int iters;
+  int converged;
+  double last_metric;
+  double res_norm;     /* ||P_Omega(T_l) - y|| after the last iteration */
+  double latency_ms;   /* submission to completion */
+  double queue_ms;     /* submission to admission */
+  char detail[128];    /* text of the CUDA error when status is TTC_ECUDA, else "" */
+} ttc_result;
+
+/* Wait up to timeout_us microseconds (negative: no limit) for a request to
+ * finish; then fill `result` (if not NULL) and copy the final cores into
+ * cores_out[k] (host buffers of r[k]*n[k]*r[k+1] doubles, or cores_out NULL)
+ * and forget the ticket.  Returns TTC_ETIMEOUT if it has not finished (the
+ * ticket stays valid), TTC_EINVAL for an unknown ticket; the request's own
+ * outcome is result->status. */
+int ttc_poll(ttc_server* s, uint64_t ticket, int64_t timeout_us, ttc_result* result,
+             double* const* cores_out);
+
+typedef struct {
+  int64_t completed;          /* requests finished with TTC_OK or TTC_ENOTCONV */
+  int64_t failed;             /* requests ended by another error */
+  int64_t queued;             /* waiting for admission now */
+  int64_t iterations;         /* request-iterations run */
+  int64_t launches;           /* kernels launched by the engine (graph kernel nodes included) */
+  double entry_iterations;    /* sum over request-iterations of |Omega| */
+  double busy_ms;             /* engine time spent in ticks (step + stop checks) */
+  double wall_ms;             /* time since creation */
+  double p50_ms, p99_ms, max_ms;   /* latency percentiles of completed requests */
+} ttc_serving_stats;
+int ttc_server_stats(ttc_server* s, ttc_serving_stats* out);
+
+/* Finish every queued and active request, stop the engine and free all.
+ * Results not polled are dropped. */
+void ttc_server_destroy(ttc_server* s);
 
 /* Allocation-free squared Frobenius distance of two tensor trains (the paper
  * has no counterpart of this call).  For callers that may not allocate

@@ -291,6 +291,8 @@ int ttc_set_observations(ttc_ctx* c, int64_t N, const int32_t* idx, const double
   P.p = (double)N / dstar;
   int s = ttc_build_layout(c, idx, y);
   if (s != TTC_OK) return s;
+  c->ynorm2 = 0.0;
+  for (int64_t e = 0; e < N; ++e) c->ynorm2 += y[e] * y[e];
   ttc_plan_tables(c);
   P.tab32 = nullptr;
   P.tab64 = nullptr;
@@ -403,80 +405,100 @@ int ttc_step(ttc_ctx* c, double alpha, ttc_step_info* out) {
   return step_impl(c, alpha, out, out != nullptr);
 }
 
+}  // extern "C"
+
+void ttc_solve_begin(ttc_ctx* c, SolveState& st) {
+  st.it = 0;
+  st.status = TTC_ENOTCONV;
+  st.done = false;
+  st.info.iters = 0;
+  st.info.converged = 0;
+  st.info.last_metric = -1.0;
+  st.info.res_norm = -1.0;
+  st.info.polish_iter = -1;
+  if (c->opt.precision == TTC_PREC_FP64) c->cur_prec = TTC_PREC_FP64;
+  if (c->opt.precision == TTC_PREC_FP32 || c->opt.precision == TTC_PREC_MIXED) c->cur_prec = TTC_PREC_FP32;
+}
+
+bool ttc_solve_needs_metric(const ttc_ctx* c, int it) {
+  const bool check = (it % c->opt.check_every == 0) || it == c->opt.max_iter;
+  return check && (c->opt.stop_rule == TTC_STOP_RELERR || c->opt.stop_rule == TTC_STOP_STEP);
+}
+
+int ttc_read_scalars(ttc_ctx* c, double* out) { return read_scalars(c, out); }
+
+void ttc_solve_after(ttc_ctx* c, SolveState& st, const double* sc, bool checked) {
+  st.info.iters = st.it;
+  unsigned flags;
+  memcpy(&flags, &sc[SC_FLAGS], sizeof(flags));
+  if (flags & 1u) {
+    st.status = TTC_ENONFINITE;
+    st.done = true;
+    return;
+  }
+  st.info.res_norm = std::sqrt(sc[SC_G2]);
+  const double rel_res = std::sqrt(sc[SC_G2] / std::fmax(c->ynorm2, 1e-300));
+  if (c->opt.precision == TTC_PREC_MIXED && c->cur_prec != TTC_PREC_FP64 && rel_res <= c->opt.polish_below) {
+    c->cur_prec = TTC_PREC_FP64;
+    st.info.polish_iter = st.it + 1;
+  }
+  const bool polishing_done = (c->opt.precision != TTC_PREC_MIXED) || c->cur_prec == TTC_PREC_FP64;
+  double metric = -1.0;
+  if (c->opt.stop_rule == TTC_STOP_RESID) {
+    metric = rel_res;
+  } else if (checked && c->opt.stop_rule == TTC_STOP_RELERR) {
+    metric = std::sqrt(std::fmax(sc[SC_METRIC], 0.0) / sc[SC_NORM]);
+  } else if (checked && c->opt.stop_rule == TTC_STOP_STEP) {
+    // ||T_{l+1} - T_l|| <= tol max(1, ||T_l||): SC_NORM holds ||T_l||^2
+    metric = std::sqrt(std::fmax(sc[SC_METRIC], 0.0)) / std::fmax(1.0, std::sqrt(sc[SC_NORM]));
+  }
+  if (metric >= 0.0) st.info.last_metric = metric;
+  if (metric >= 0.0 && metric <= c->opt.tol && polishing_done) {
+    st.info.converged = 1;
+    st.status = TTC_OK;
+    st.done = true;
+    return;
+  }
+  if (st.it >= c->opt.max_iter) {
+    if (c->opt.stop_rule == TTC_STOP_NONE) {
+      st.info.converged = 1;
+      st.status = TTC_OK;
+    }
+    st.done = true;
+  }
+}
+
+extern "C" {
+
 int ttc_solve(ttc_ctx* c, ttc_solve_info* out) {
   if (!c) return TTC_EINVAL;
+  if (!c->have_obs || !c->have_cores) return TTC_EINVAL;
   if (c->opt.stop_rule == TTC_STOP_RELERR && !c->hp.has_truth) return TTC_EINVAL;
   TTC_TRY(set_scalar(c, SC_ALPHA_OVR, 0.0));
   c->alpha_ovr = 0.0;
-  double ynorm2 = 0.0;
-  {
-    // ||y||^2 for the relative residual that triggers the FP64 polish
-    std::vector<double> y(c->N);
-    TTC_CUDA(cudaMemcpy(y.data(), c->hp.y64[0], sizeof(double) * c->N, cudaMemcpyDeviceToHost));
-    for (double v : y) ynorm2 += v * v;
-  }
-  ttc_solve_info info;
-  info.iters = 0;
-  info.converged = 0;
-  info.last_metric = -1.0;
-  info.res_norm = -1.0;
-  info.polish_iter = -1;
-  if (c->opt.precision == TTC_PREC_FP64) c->cur_prec = TTC_PREC_FP64;
-  if (c->opt.precision == TTC_PREC_FP32 || c->opt.precision == TTC_PREC_MIXED) c->cur_prec = TTC_PREC_FP32;
-  int status = TTC_ENOTCONV;
-  for (int it = 1; it <= c->opt.max_iter; ++it) {
-    bool check = (it % c->opt.check_every == 0) || it == c->opt.max_iter;
-    bool need_sync = check || c->opt.precision == TTC_PREC_MIXED;
+  SolveState st;
+  ttc_solve_begin(c, st);
+  // scalars are read back every check, and every iteration in MIXED mode
+  // (the FP64 switch) or with the residual rule
+  const bool every = c->opt.precision == TTC_PREC_MIXED || c->opt.stop_rule == TTC_STOP_RESID;
+  while (!st.done) {
+    ++st.it;
     int s = step_impl(c, 0.0, nullptr, false);
     if (s != TTC_OK) {
-      status = s;
+      st.status = s;
       break;
     }
-    info.iters = it;
-    if (!need_sync) continue;
-    if (check && c->opt.stop_rule != TTC_STOP_NONE) {
-      TTC_TRY(ttc_launch_metric(c, c->opt.stop_rule == TTC_STOP_RELERR ? 0 : 1));
-    }
+    const bool check = (st.it % c->opt.check_every == 0) || st.it == c->opt.max_iter;
+    if (!check && !every) continue;
+    const bool metric = ttc_solve_needs_metric(c, st.it);
+    if (metric) TTC_TRY(ttc_launch_metric(c, c->opt.stop_rule == TTC_STOP_RELERR ? 0 : 1));
     double sc[SC_COUNT];
     TTC_TRY(read_scalars(c, sc));
-    unsigned flags;
-    memcpy(&flags, &sc[SC_FLAGS], sizeof(flags));
-    if (flags & 1u) {
-      status = TTC_ENONFINITE;
-      break;
-    }
-    info.res_norm = std::sqrt(sc[SC_G2]);
-    if (c->opt.precision == TTC_PREC_MIXED && c->cur_prec != TTC_PREC_FP64 &&
-        sc[SC_G2] <= c->opt.polish_below * c->opt.polish_below * ynorm2) {
-      c->cur_prec = TTC_PREC_FP64;
-      info.polish_iter = it + 1;
-    }
-    if (check) {
-      if (c->opt.stop_rule == TTC_STOP_NONE) {
-        if (it == c->opt.max_iter) {
-          status = TTC_OK;
-          info.converged = 1;
-        }
-        continue;
-      }
-      double metric;
-      if (c->opt.stop_rule == TTC_STOP_RELERR) {
-        metric = std::sqrt(std::fmax(sc[SC_METRIC], 0.0) / sc[SC_NORM]);
-      } else {
-        // ||T_{l+1} - T_l|| <= tol max(1, ||T_l||): SC_NORM holds ||T_l||^2
-        metric = std::sqrt(std::fmax(sc[SC_METRIC], 0.0)) / std::fmax(1.0, std::sqrt(sc[SC_NORM]));
-      }
-      info.last_metric = metric;
-      bool polishing_done = (c->opt.precision != TTC_PREC_MIXED) || c->cur_prec == TTC_PREC_FP64;
-      if (metric <= c->opt.tol && polishing_done) {
-        info.converged = 1;
-        status = TTC_OK;
-        break;
-      }
-    }
+    ttc_solve_after(c, st, sc, metric);
   }
-  if (out) *out = info;
-  return status;
+  st.info.iters = st.it;
+  if (out) *out = st.info;
+  return st.status;
 }
 
 int ttc_relerr(ttc_ctx* c, double* out) {

@@ -228,7 +228,15 @@ int ttc_batch_step(ttc_batch* b) {
   if (stale) TTC_TRY(capture(b));
   TTC_CUDA(cudaGraphLaunch(b->exec, b->stream));
   b->nlaunch += b->kernels_per_step;
-  for (auto* c : b->members) ++c->iter;
+  for (auto* c : b->members) {
+    ++c->iter;
+    if (c->opt.eps_frozen && !c->eps_set) {
+      // the first iteration's epsilon stays fixed from here on
+      TTC_CUDA(cudaMemcpyAsync(c->hp.scal + SC_EPS_FIXED, c->hp.scal + SC_EPS, sizeof(double),
+                               cudaMemcpyDeviceToDevice, b->stream));
+      c->eps_set = true;
+    }
+  }
   if (b->prof) {
     TTC_CUDA(cudaEventSynchronize(b->ev_end));
     float t = 0.f;

@@ -49,7 +49,22 @@ struct ttc_ctx {
   bool eps_set = false;
   int cur_prec = TTC_PREC_FP64;    // precision of the Omega pass for the next step
   double alpha_ovr = 0.0;           // step-size override currently on the device
+  double ynorm2 = 0.0;              // ||y||^2 of the observations
 };
+
+// the solver's per-iteration bookkeeping (shared by ttc_solve and the server)
+struct SolveState {
+  int it = 0;
+  int status = TTC_ENOTCONV;
+  bool done = false;
+  ttc_solve_info info;
+};
+void ttc_solve_begin(ttc_ctx* c, SolveState& st);
+// after iteration st.it (scalars already read into sc, metric computed if the
+// rule needed it this iteration): precision switch and stop decision
+void ttc_solve_after(ttc_ctx* c, SolveState& st, const double* sc, bool checked);
+bool ttc_solve_needs_metric(const ttc_ctx* c, int it);
+int ttc_read_scalars(ttc_ctx* c, double* out);
 
 // allocation helpers (api.cu)
 int ttc_alloc(ttc_ctx* c, void** p, size_t bytes, bool obs);

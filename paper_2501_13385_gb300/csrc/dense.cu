@@ -821,7 +821,19 @@ int ttc_alloc_dense(ttc_ctx* c) {
   size_t bond_need = sizeof(double) * (size_t)(2 * qmax * qmax + 5 * qmax * rmax + 6 * rmax * rmax + kThreads) +
                      sizeof(float) * (size_t)(2 * rmax * rmax);
   pl.smem_stage = std::max(red_need, std::max(proj_need, bond_need)) + 64;
-  TTC_CUDA(cudaFuncSetAttribute(k_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem_stage));
+  {
+    // the attribute is per device and shared by every context: only raise it,
+    // so that contexts needing more than this one keep launching
+    static std::mutex mu;
+    static std::map<int, size_t> granted;
+    std::lock_guard<std::mutex> lk(mu);
+    int dev = 0;
+    TTC_CUDA(cudaGetDevice(&dev));
+    if (granted[dev] < pl.smem_stage) {
+      TTC_CUDA(cudaFuncSetAttribute(k_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem_stage));
+      granted[dev] = pl.smem_stage;
+    }
+  }
   plan_of(c) = pl;
   return TTC_OK;
 }

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libttc.so")
 
 PREC_FP64, PREC_MIXED, PREC_FP32 = 0, 1, 2
-STOP_RELERR, STOP_STEP, STOP_NONE = 0, 1, 2
+STOP_RELERR, STOP_STEP, STOP_NONE, STOP_RESID = 0, 1, 2, 3
 
 STATUS = {
     0: "TTC_OK", -1: "TTC_EINVAL", -2: "TTC_ENOMEM", -3: "TTC_ERANGE", -4: "TTC_EDUP",
@@ -52,6 +52,28 @@ class SolveInfo(C.Structure):
                 ("res_norm", C.c_double), ("polish_iter", C.c_int)]
 
 
+class Request(C.Structure):
+    _fields_ = [
+        ("d", C.c_int), ("n", C.POINTER(C.c_int64)), ("r", C.POINTER(C.c_int32)), ("N", C.c_int64),
+        ("idx", C.POINTER(C.c_int32)), ("y", C.POINTER(C.c_double)),
+        ("init", C.POINTER(C.POINTER(C.c_double))), ("truth_r", C.POINTER(C.c_int32)),
+        ("truth", C.POINTER(C.POINTER(C.c_double))), ("opt", C.POINTER(Options)),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("converged", C.c_int), ("last_metric", C.c_double),
+                ("res_norm", C.c_double), ("latency_ms", C.c_double), ("queue_ms", C.c_double),
+                ("detail", C.c_char * 128)]
+
+
+class ServingStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("queued", C.c_int64),
+                ("iterations", C.c_int64), ("launches", C.c_int64), ("entry_iterations", C.c_double),
+                ("busy_ms", C.c_double), ("wall_ms", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("max_ms", C.c_double)]
+
+
 _lib = None
 
 EXPORTS = [
@@ -61,6 +83,7 @@ EXPORTS = [
     "ttc_device_bytes", "ttc_destroy", "ttc_strerror", "ttc_last_cuda_error", "ttc_launch_count",
     "ttc_tt_dist2_static", "ttc_batch_create", "ttc_batch_step", "ttc_batch_sync", "ttc_batch_profile_enable",
     "ttc_batch_profile_read", "ttc_batch_launch_count", "ttc_batch_destroy",
+    "ttc_server_create", "ttc_submit", "ttc_poll", "ttc_server_stats", "ttc_server_destroy",
 ]
 
 
@@ -103,6 +126,11 @@ def lib():
         "ttc_batch_profile_read": (C.c_int, [vp, dp, i64p, C.c_int]),
         "ttc_batch_launch_count": (C.c_int, [vp, i64p]),
         "ttc_batch_destroy": (None, [vp]),
+        "ttc_server_create": (C.c_int, [C.POINTER(vp), C.c_size_t, C.c_int, vp]),
+        "ttc_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+        "ttc_poll": (C.c_int, [vp, C.c_uint64, C.c_int64, C.POINTER(Result), dpp]),
+        "ttc_server_stats": (C.c_int, [vp, C.POINTER(ServingStats)]),
+        "ttc_server_destroy": (None, [vp]),
         "ttc_strerror": (C.c_char_p, [C.c_int]),
         "ttc_last_cuda_error": (C.c_char_p, []),
     }
@@ -323,6 +351,93 @@ class Batch:
     def close(self):
         if self._h:
             lib().ttc_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Continuous-batching solver service (ttc_server_*): submit requests,
+    poll for their results.  The engine thread runs inside the library."""
+
+    def __init__(self, budget_bytes: int = 0, max_slots: int = 64, stream: Optional[int] = None):
+        self._h = C.c_void_p()
+        self._shapes = {}
+        _check(lib().ttc_server_create(C.byref(self._h), int(budget_bytes), int(max_slots),
+                                       C.c_void_p(stream) if stream else None), "ttc_server_create")
+
+    def submit(self, n, r, idx, y, init, truth=None, options: Optional[Options] = None) -> int:
+        m = len(n)
+        na = np.ascontiguousarray(n, dtype=np.int64)
+        ra = np.ascontiguousarray(r, dtype=np.int32)
+        idx, ip = _i32(idx)
+        y, yp = _f64(y)
+        if idx.ndim != 2 or idx.shape[1] != m or y.shape[0] != idx.shape[0]:
+            raise ValueError("idx must be (N, d) and y (N,)")
+        keep = [na, ra, idx, y]
+        dptr = C.POINTER(C.c_double)
+        cores = [np.ascontiguousarray(c, dtype=np.float64) for c in init]
+        for k, c in enumerate(cores):
+            if c.shape != (r[k], n[k], r[k + 1]):
+                raise ValueError(f"core {k} has shape {c.shape}")
+        init_p = (dptr * m)(*[c.ctypes.data_as(dptr) for c in cores])
+        keep += cores
+        req = Request(d=m, n=na.ctypes.data_as(C.POINTER(C.c_int64)), r=ra.ctypes.data_as(C.POINTER(C.c_int32)),
+                      N=idx.shape[0], idx=ip, y=yp, init=init_p)
+        if truth is not None:
+            rt = np.asarray([1] + [int(c.shape[2]) for c in truth[:-1]] + [1], dtype=np.int32)
+            tc = [np.ascontiguousarray(c, dtype=np.float64) for c in truth]
+            keep += [rt] + tc
+            req.truth_r = rt.ctypes.data_as(C.POINTER(C.c_int32))
+            req.truth = (dptr * m)(*[c.ctypes.data_as(dptr) for c in tc])
+        if options is not None:
+            req.opt = C.pointer(options)
+        t = C.c_uint64()
+        _check(lib().ttc_submit(self._h, C.byref(req), C.byref(t)), "ttc_submit")
+        self._shapes[t.value] = (list(n), list(r))
+        del keep
+        return t.value
+
+    def poll(self, ticket: int, timeout_s: Optional[float] = None, cores: bool = True):
+        """Result dict (with the final cores), or None if not finished within
+        timeout_s (None: wait without limit)."""
+        n, r = self._shapes.get(ticket, (None, None))
+        cores = cores and n is not None
+        res = Result()
+        arrs = [np.empty((r[k], n[k], r[k + 1])) for k in range(len(n))] if cores else None
+        dptr = C.POINTER(C.c_double)
+        ptrs = (dptr * len(n))(*[a.ctypes.data_as(dptr) for a in arrs]) if cores else None
+        us = -1 if timeout_s is None else int(timeout_s * 1e6)
+        st = lib().ttc_poll(self._h, ticket, us, C.byref(res), ptrs)
+        if st == -7:
+            return None
+        _check(st, "ttc_poll")
+        self._shapes.pop(ticket, None)
+        out = {"status": STATUS.get(res.status, res.status), "iters": res.iters, "converged": bool(res.converged),
+               "last_metric": res.last_metric, "res_norm": res.res_norm, "latency_ms": res.latency_ms,
+               "queue_ms": res.queue_ms, "detail": res.detail.decode(errors="replace")}
+        if cores and res.status in (0, -6):
+            out["cores"] = arrs
+        return out
+
+    def stats(self) -> dict:
+        v = ServingStats()
+        _check(lib().ttc_server_stats(self._h, C.byref(v)), "ttc_server_stats")
+        return {f: getattr(v, f) for f, _ in ServingStats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().ttc_server_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

@@ -81,3 +81,17 @@ def test_batch_rejects_bad_members():
         ttc.Batch([c, empty])
     empty.close()
     c.close()
+
+
+def test_contexts_of_different_ranks_coexist():
+    # a context needing less shared memory, created later, must not break
+    # the launches of an earlier one that needs more
+    P_big, big = make(MEMBERS[5][0], ttc.PREC_FP32, 400)
+    P_small, small = make(MEMBERS[2][0], ttc.PREC_FP32, 401)
+    ref = make(MEMBERS[5][0], ttc.PREC_FP32, 400)[1]
+    for c in (big, small, ref):
+        c.step()
+    for a, b in zip(big.get_cores(), ref.get_cores()):
+        assert np.array_equal(a, b)
+    for c in (big, small, ref):
+        c.close()

@@ -202,6 +202,7 @@ int ttc_create(ttc_ctx** out, int d, const int64_t* n, const int32_t* r, const t
   for (int k = 0; k < d; ++k) c->n[k] = n[k];
   for (int k = 0; k <= d; ++k) c->r[k] = r[k];
   c->rank_bucket = rmax <= 4 ? 4 : rmax <= 8 ? 8 : rmax <= 16 ? 16 : 32;
+  c->rank_max = rmax;
   memset(&c->hp, 0, sizeof(DevProb));
   DevProb& P = c->hp;
   P.m = d;

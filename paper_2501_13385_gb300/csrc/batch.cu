@@ -69,7 +69,7 @@ int build_groups(ttc_batch* b) {
       if (prec != key.first || c->rank_bucket != key.second) continue;
       G.idx.push_back(i);
       descs.push_back(c->hp);
-      pb.push_back(pb.back() + c->hp.chunk_base[c->m]);
+      pb.push_back(pb.back() + ttc_pass_blocks(c->hp, key.second));
       int nseg = 0;
       for (int k = 0; k < c->m; ++k) nseg += c->hp.n[k];
       sb.push_back(sb.back() + nseg);
@@ -91,6 +91,8 @@ int build_groups(ttc_batch* b) {
     }
     G.g.prec = key.first;
     G.g.R = key.second;
+    G.g.RC = 1;
+    for (int i : G.idx) G.g.RC = std::max(G.g.RC, b->members[i]->rank_max);
     G.g.nprob = (int)descs.size();
     G.g.probs = G.probs;
     G.g.pass_base = G.pass_base;

@@ -45,14 +45,19 @@ struct DevProb {
 
   // interface tables: prefix L_j(x_0..x_{j-1}) = T_0(x_0)...T_{j-1}(x_{j-1})
   // (a row of length r_j) and suffix R_j(x_j..x_{d-1}) = T_j(x_j)...T_{d-1}(x_{d-1})
-  // (a column of length r_j), for all index combinations, row-major mixed
-  // radix with the lowest mode most significant; row g at g * R (padded)
+  // (a column of length r_j), for all index combinations.  A table covers
+  // modes whose code fields share one 32-bit word; its row index is those
+  // fields as they sit in the word (the lowest mode in the lowest bits), so
+  // rows of coordinates >= n_j exist but are never read.  Row g at g * R.
   int ntab;
   int tab_side[2 * TTC_MAXM];     // 0 prefix, 1 suffix
   int tab_j[2 * TTC_MAXM];
   long long tab_rows[2 * TTC_MAXM];
   long long tab_row0[2 * TTC_MAXM];
   long long tab_total;
+  int tab_word[2 * TTC_MAXM];     // table row = (code word tab_word >> tab_shift) & (2^tab_bits - 1):
+  int tab_shift[2 * TTC_MAXM];    // the bit-concatenated coordinates of the table's modes
+  int tab_bits[2 * TTC_MAXM];
   int pre_tab[TTC_MAXM];          // mode k: table giving the prefix over modes < k (-1: none)
   int suf_tab[TTC_MAXM];          // mode k: table giving the suffix over modes > k (-1: none)
   float* tab32;

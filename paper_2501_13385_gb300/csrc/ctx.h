@@ -22,7 +22,8 @@ struct ttc_ctx {
   int N = 0;
   bool have_obs = false;
   bool have_cores = false;
-  int rank_bucket = 4;             // compile-time rank bound used by the Omega-pass kernels
+  int rank_bucket = 4;             // row stride of the padded core mirrors and tables (4, 8, 16, 32)
+  int rank_max = 1;                // largest TT-rank: register size of the small-rank pass
 
   DevProb hp;                       // host mirror of the descriptor
   DevProb* dp = nullptr;            // device copy
@@ -84,9 +85,31 @@ struct BatchGroup {
   const int* pass_base;      // device [nprob + 1]: block offsets of the sampled pass
   const int* seg_base;       // device [nprob + 1]: block offsets of the slice reduction
   const long long* tab_base; // device [nprob + 1]: row offsets of the interface tables
+  int RC;                    // register size of the pass: the members' largest TT-rank
   int pass_blocks, seg_blocks;
   long long tab_rows;
 };
+
+// blocks of one sampled pass: small rank buckets (R <= 8) reduce one chunk
+// per warp, larger ones one chunk per block
+inline int ttc_pass_blocks(const DevProb& P, int R) {
+  const int chunks = P.chunk_base[P.m];
+  return R <= 8 ? (chunks + TTC_NT / 32 - 1) / (TTC_NT / 32) : chunks;
+}
+
+// one launch of the sampled-pass kernel: a single problem (g == nullptr)
+// or a batch group
+struct PassLaunch {
+  const DevProb* P;
+  const BatchGroup* g;
+  cudaStream_t st;
+};
+// pass_small_f32.cu / pass_small_f64.cu: rank buckets 4 and 8, register size
+// RC = the largest TT-rank (1..8); pass_large.cu: buckets 16 and 32
+int ttc_pass_small_f32(int RC, const PassLaunch& L);
+int ttc_pass_small_f64(int RC, const PassLaunch& L);
+int ttc_pass_large(bool f32, int R, const PassLaunch& L);
+int ttc_pass_opt_in_large();
 
 // omega_pass.cu
 int ttc_launch_omega_pass_batch(const BatchGroup& g, cudaStream_t st, int phase);   // 0: pass, 1: slice reduction, 2: tables

@@ -1,0 +1,670 @@
+// Device code of the sampled pass over Omega, one pass per mode k
+// (Algorithm 2, first lines, with the sparse factor of Lemma 3.5
+// Eq. (tsp in nm)):
+//   v_w  = T_1(x_1) ... T_d(x_d)                   (Eq. (TT Core))
+//   g_w  = v_w - y_w                               (entries of G_l = P_Omega(T_l - T*))
+//   s_k(x)  = sum_{w : x_k = x} g_w^2              (diag(M_k(G_l) M_k(G_l)^T), Section 3.2)
+//   E_k(x)  = sum_{w : x_k = x} g_w l_{k-1}(w)^T r_{k+1}(w)^T
+// with l_{k-1} = T^{<=k-1}(x_<k) and r_{k+1} = T^{>=k+1}(x_>k) the interfaces
+// of the iterate's own cores.  The weights of the metric are constant on a
+// mode-k slice, so they are applied after the reduction (dense stage).
+//
+// Layout: entries of mode k are stored in mode-k order, so a slice x is a
+// contiguous segment; segments are cut into chunks of TTC_CHUNK entries, each
+// reduced by one warp (small ranks) or one block (large ranks) without
+// atomics; a second kernel sums the chunk partials of each slice in chunk
+// order in FP64.  Core slices are read from padded mirrors (row stride R =
+// rank bucket, 16-byte aligned) with 16-byte loads; the pass's own slice is
+// constant on a chunk and sits in shared memory.
+//
+// Two compile-time sizes: R, the row stride of the padded storage (4, 8, 16,
+// 32), and RC <= R, the size of the register arrays (the largest TT-rank of
+// the problem for small ranks, R for large).  Loops stop at the runtime ranks
+// of each mode, so a problem computes the same values, bitwise, with any RC
+// at least its largest rank.  Results are reproducible for a given layout.
+#pragma once
+
+#include "ctx.h"
+
+namespace ttc_pass {
+
+template <typename T>
+__device__ __forceinline__ const T* core_ptr(const DevProb& P, int k);
+template <>
+__device__ __forceinline__ const float* core_ptr<float>(const DevProb& P, int k) { return P.core32p[k]; }
+template <>
+__device__ __forceinline__ const double* core_ptr<double>(const DevProb& P, int k) { return P.core64p[k]; }
+
+template <typename T>
+__device__ __forceinline__ T yval(const DevProb& P, int k, int j);
+template <>
+__device__ __forceinline__ float yval<float>(const DevProb& P, int k, int j) { return __ldg(P.y32[k] + j); }
+template <>
+__device__ __forceinline__ double yval<double>(const DevProb& P, int k, int j) { return __ldg(P.y64[k] + j); }
+
+template <typename T>
+__device__ __forceinline__ T* tab_ptr(const DevProb& P);
+template <>
+__device__ __forceinline__ float* tab_ptr<float>(const DevProb& P) { return P.tab32; }
+template <>
+__device__ __forceinline__ double* tab_ptr<double>(const DevProb& P) { return P.tab64; }
+
+// 16-byte loads of the first min(len, RC) entries of a zero-padded row whose
+// storage is padded to a multiple of 4 floats / 2 doubles at least RC long
+// (so every vector read stays inside the row).  Entries from len on are left
+// as they are: callers pass zero-initialised arrays.  Global rows go through
+// the read-only path, shared rows are read directly.
+template <int RC, bool kGlobal>
+__device__ __forceinline__ void load_row(const float* __restrict__ row, int len, float (&out)[RC]) {
+#pragma unroll
+  for (int b = 0; b < RC; b += 4) {
+    if (b >= len) break;
+    const float4 v = kGlobal ? __ldg(reinterpret_cast<const float4*>(row + b))
+                             : *reinterpret_cast<const float4*>(row + b);
+    out[b] = v.x;
+    if (b + 1 < RC) out[b + 1] = v.y;
+    if (b + 2 < RC) out[b + 2] = v.z;
+    if (b + 3 < RC) out[b + 3] = v.w;
+  }
+}
+template <int RC, bool kGlobal>
+__device__ __forceinline__ void load_row(const double* __restrict__ row, int len, double (&out)[RC]) {
+#pragma unroll
+  for (int b = 0; b < RC; b += 2) {
+    if (b >= len) break;
+    const double2 v = kGlobal ? __ldg(reinterpret_cast<const double2*>(row + b))
+                              : *reinterpret_cast<const double2*>(row + b);
+    out[b] = v.x;
+    if (b + 1 < RC) out[b + 1] = v.y;
+  }
+}
+
+template <typename T, int RC>
+__device__ __forceinline__ void zero(T (&v)[RC]) {
+#pragma unroll
+  for (int a = 0; a < RC; ++a) v[a] = 0;
+}
+
+// l <- l T_j(x): row vector times an ra x rb slice (padded layout, stride R)
+template <typename T, int R, int RC>
+__device__ __forceinline__ void row_times(const DevProb& P, int j, int x, T (&l)[RC]) {
+  const int ra = P.r[j], rb = P.r[j + 1];
+  const T* S = core_ptr<T>(P, j) + (long long)x * R * R;
+  T out[RC], row[RC];
+  zero(out);
+  zero(row);
+  if (rb == 1) {   // the slice is one contiguous column
+    load_row<RC, true>(S, ra, row);
+    T acc = 0;
+#pragma unroll
+    for (int a = 0; a < RC; ++a) {
+      if (a >= ra) break;
+      acc = fma(l[a], row[a], acc);
+    }
+    out[0] = acc;
+  } else {
+#pragma unroll
+    for (int a = 0; a < RC; ++a) {
+      if (a >= ra) break;
+      load_row<RC, true>(S + a * R, rb, row);
+#pragma unroll
+      for (int b = 0; b < RC; ++b) {
+        if (b >= rb) break;
+        out[b] = fma(l[a], row[b], out[b]);
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < RC; ++b) l[b] = out[b];
+}
+
+// rho <- T_j(x) rho: an ra x rb slice times a column vector (padded layout)
+template <typename T, int R, int RC>
+__device__ __forceinline__ void times_col(const DevProb& P, int j, int x, T (&rho)[RC]) {
+  const int ra = P.r[j], rb = P.r[j + 1];
+  const T* S = core_ptr<T>(P, j) + (long long)x * R * R;
+  T out[RC], row[RC];
+  zero(out);
+  zero(row);
+  if (rb == 1) {
+    load_row<RC, true>(S, ra, row);
+#pragma unroll
+    for (int a = 0; a < RC; ++a) {
+      if (a >= ra) break;
+      out[a] = row[a] * rho[0];
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < RC; ++a) {
+      if (a >= ra) break;
+      load_row<RC, true>(S + a * R, rb, row);
+      T acc = 0;
+#pragma unroll
+      for (int b = 0; b < RC; ++b) {
+        if (b >= rb) break;
+        acc = fma(row[b], rho[b], acc);
+      }
+      out[a] = acc;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < RC; ++a) rho[a] = out[a];
+}
+
+// l^T Ts r for the pass's own slice Ts (ra x rb, row stride R, zero-padded)
+// in shared memory, a row at a time with 16-byte loads (the same rows for
+// every lane: broadcasts)
+template <typename T, int R, int RC>
+__device__ __forceinline__ T slice_value(const T* Ts, int ra, int rb, const T (&lv)[RC], const T (&rv)[RC]) {
+  T v = 0;
+#pragma unroll
+  for (int a = 0; a < RC; ++a) {
+    if (a >= ra) break;
+    T row[RC];
+    zero(row);
+    load_row<RC, false>(Ts + a * R, rb, row);
+    T acc = 0;
+#pragma unroll
+    for (int b = 0; b < RC; ++b) {
+      if (b >= rb) break;
+      acc = fma(row[b], rv[b], acc);
+    }
+    v = fma(lv[a], acc, v);
+  }
+  return v;
+}
+
+// row of interface table t for an entry: its modes' bit fields
+__device__ __forceinline__ int tab_index(const DevProb& P, const Code& words, int t) {
+  return (int)((words.word(P.tab_word[t]) >> P.tab_shift[t]) & ((1u << P.tab_bits[t]) - 1u));
+}
+
+// left interface (modes < k), right interface (modes > k) and the entry
+// value.  Where an interface table covers a run of modes, one table row
+// (stride R) replaces that part of the chain.
+template <typename T, int R, int RC>
+__device__ __forceinline__ T interfaces(const DevProb& P, int k, const Code& words, const T* Ts, T (&lv)[RC],
+                                        T (&rv)[RC]) {
+  zero(lv);
+  zero(rv);
+  lv[0] = 1;
+  rv[0] = 1;
+  int j0 = 0;
+  const int tl = P.pre_tab[k];
+  if (tl >= 0) {
+    const int jt = P.tab_j[tl];
+    load_row<RC, true>(tab_ptr<T>(P) + (P.tab_row0[tl] + tab_index(P, words, tl)) * R, P.r[jt], lv);
+    j0 = jt;
+  }
+  for (int j = j0; j < k; ++j) row_times<T, R, RC>(P, j, code_coord(P, words, j), lv);
+  int j1 = P.m;
+  const int tr = P.suf_tab[k];
+  if (tr >= 0) {
+    const int jt = P.tab_j[tr];
+    load_row<RC, true>(tab_ptr<T>(P) + (P.tab_row0[tr] + tab_index(P, words, tr)) * R, P.r[jt], rv);
+    j1 = jt;
+  }
+  for (int j = j1 - 1; j > k; --j) times_col<T, R, RC>(P, j, code_coord(P, words, j), rv);
+  return slice_value<T, R, RC>(Ts, P.r[k], P.r[k + 1], lv, rv);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int kEPT = TTC_CHUNK / TTC_NT;   // entries per thread (large ranks)
+constexpr int kWarps = TTC_NT / 32;         // chunks per block (small ranks)
+
+__host__ __device__ constexpr int pow2_at_least(int n) { return n <= 1 ? 1 : 2 * pow2_at_least((n + 1) / 2); }
+__host__ __device__ constexpr int log2_exact(int n) { return n <= 1 ? 0 : 1 + log2_exact(n / 2); }
+
+// Sum of N = 2^p per-lane values over the 32 lanes of a warp by a halving
+// butterfly.  While more than one value is left, the step with offset o has
+// every lane keep one half of its values, send the other half to lane ^ o
+// and add what it receives; the remaining offsets sum the last value.
+// Afterwards v[0] (and v[1] when N = 64) of lane L hold the totals of value
+// L >> (5 - p) (N <= 32) or of values 2L and 2L+1 (N = 64).  Every total is
+// the same balanced tree over the lanes whatever N is.
+template <typename T, int N, int C, int O>
+__device__ __forceinline__ void butterfly_step(T (&v)[N], int lane) {
+  if constexpr (O >= 1) {
+    if constexpr (C >= 2) {
+      const bool up = (lane & O) != 0;
+      constexpr int h = C / 2;
+#pragma unroll
+      for (int i = 0; i < h; ++i) {
+        const T send = up ? v[i] : v[i + h];
+        const T keep = up ? v[i + h] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+      }
+      butterfly_step<T, N, h, O / 2>(v, lane);
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
+      butterfly_step<T, N, 1, O / 2>(v, lane);
+    }
+  }
+}
+
+// Sums the per-lane accumulators of a warp and writes the chunk partial
+// out[1 + a*rb + b].  Accumulator i stands for (a, b) = (0, i) when KIND is 0
+// (first mode, r_{k-1} = 1), (i, 0) when KIND is 1 (last mode, r_k = 1) and
+// (i / RC, i % RC) otherwise.
+template <typename T, int NV, int KIND, int RC>
+__device__ __forceinline__ void store_partials(T (&acc)[NV], int lane, T* out, int ra, int rb) {
+  butterfly_step<T, NV, NV, 16>(acc, lane);
+  auto put = [&](int o, T v) {
+    int a, b;
+    if constexpr (KIND == 0) {
+      a = 0;
+      b = o;
+    } else if constexpr (KIND == 1) {
+      a = o;
+      b = 0;
+    } else {
+      a = o / RC;
+      b = o % RC;
+    }
+    if (a < ra && b < rb) out[1 + a * rb + b] = v;
+  };
+  if constexpr (NV == 64) {
+    put(2 * lane, acc[0]);
+    put(2 * lane + 1, acc[1]);
+  } else {
+    constexpr int sh = 5 - log2_exact(NV);
+    if ((lane & ((1 << sh) - 1)) == 0) put(lane >> sh, acc[0]);
+  }
+}
+
+// where an interface comes from as one padded row: row index = a bit field
+// of the entry's code, row at base + index * stride
+template <typename T>
+struct RowSrc {
+  const T* base;
+  int word, shift;
+  unsigned mask;
+  int stride;
+};
+template <typename T>
+__device__ __forceinline__ const T* row_of(const RowSrc<T>& s, const Code& w) {
+  return s.base + (long long)((w.word(s.word) >> s.shift) & s.mask) * s.stride;
+}
+
+// The left interface of mode k as one row: the prefix table over exactly
+// modes 0..k-1, or core 0's slice when k = 1 (a 1 x r_1 row)
+template <typename T>
+__device__ __forceinline__ bool left_src(const DevProb& P, int k, RowSrc<T>& s) {
+  const int t = P.pre_tab[k];
+  if (t >= 0 && P.tab_j[t] == k) {
+    s = {tab_ptr<T>(P) + P.tab_row0[t] * P.R, P.tab_word[t], P.tab_shift[t], (1u << P.tab_bits[t]) - 1u, P.R};
+    return true;
+  }
+  if (k == 1) {
+    s = {core_ptr<T>(P, 0), P.cword[0], P.cshift[0], (1u << P.cbits[0]) - 1u, P.R * P.R};
+    return true;
+  }
+  return false;
+}
+// The right interface of mode k as one row: the suffix table over exactly
+// modes k+1..d-1, or the last core's slice when k = d-2 (an r_{d-1} column,
+// stored contiguously)
+template <typename T>
+__device__ __forceinline__ bool right_src(const DevProb& P, int k, RowSrc<T>& s) {
+  const int t = P.suf_tab[k];
+  if (t >= 0 && P.tab_j[t] == k + 1) {
+    s = {tab_ptr<T>(P) + P.tab_row0[t] * P.R, P.tab_word[t], P.tab_shift[t], (1u << P.tab_bits[t]) - 1u, P.R};
+    return true;
+  }
+  if (k == P.m - 2) {
+    const int j = P.m - 1;
+    s = {core_ptr<T>(P, j), P.cword[j], P.cshift[j], (1u << P.cbits[j]) - 1u, P.R * P.R};
+    return true;
+  }
+  return false;
+}
+
+// One chunk whose interfaces are each one row (or the identity at the ends
+// of the train).  Loops run over the full register size RC: rows, slices and
+// tables are zero-padded, so the extra terms add exact zeros.
+// KIND 0: first mode (l = 1), KIND 1: last mode (r = 1), KIND 2: interior.
+template <typename T, int R, int RC, int KIND>
+__device__ __forceinline__ void warp_chunk_rows(const DevProb& P, int k, int beg, int end, const T* Ts,
+                                                const RowSrc<T>& ls, const RowSrc<T>& rs, T* out) {
+  const int lane = threadIdx.x & 31;
+  constexpr int NV = pow2_at_least(KIND == 2 ? RC * RC : RC);
+  T acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0;
+  T tv[RC];   // KIND 0: the slice's row, KIND 1: its column (registers)
+  zero(tv);
+  if constexpr (KIND == 0) load_row<RC, false>(Ts, RC, tv);
+  if constexpr (KIND == 1) {
+#pragma unroll
+    for (int a = 0; a < RC; ++a) tv[a] = Ts[a * R];
+  }
+  T s2 = 0;
+  const bool keep = P.keep_residual && k == 0;
+  int e = beg + lane;
+  Code nxt_words = {0u, 0u, 0u, 0u};
+  T nxt_y = 0;
+  if (e < end) {
+    nxt_words = load_code(P, k, e);
+    nxt_y = yval<T>(P, k, e);
+  }
+  for (; e < end; e += 32) {
+    const Code words = nxt_words;
+    const T yv = nxt_y;
+    if (e + 32 < end) {
+      nxt_words = load_code(P, k, e + 32);
+      nxt_y = yval<T>(P, k, e + 32);
+    }
+    T lv[RC], rv[RC];
+    zero(lv);
+    zero(rv);
+    if constexpr (KIND != 0) load_row<RC, true>(row_of(ls, words), RC, lv);
+    if constexpr (KIND != 1) load_row<RC, true>(row_of(rs, words), RC, rv);
+    T v = 0;
+    if constexpr (KIND == 0) {
+#pragma unroll
+      for (int b = 0; b < RC; ++b) v = fma(tv[b], rv[b], v);
+    } else if constexpr (KIND == 1) {
+#pragma unroll
+      for (int a = 0; a < RC; ++a) v = fma(lv[a], tv[a], v);
+    } else {
+#pragma unroll
+      for (int a = 0; a < RC; ++a) {
+        T row[RC];
+        zero(row);
+        load_row<RC, false>(Ts + a * R, RC, row);
+        T t = 0;
+#pragma unroll
+        for (int b = 0; b < RC; ++b) t = fma(row[b], rv[b], t);
+        v = fma(lv[a], t, v);
+      }
+    }
+    const T g = v - yv;
+    if (keep) P.g[P.perm[0][e]] = (double)g;
+    s2 = fma(g, g, s2);
+    if constexpr (KIND == 0) {
+#pragma unroll
+      for (int b = 0; b < RC; ++b) acc[b] = fma(g, rv[b], acc[b]);
+    } else if constexpr (KIND == 1) {
+#pragma unroll
+      for (int a = 0; a < RC; ++a) acc[a] = fma(g, lv[a], acc[a]);
+    } else {
+#pragma unroll
+      for (int a = 0; a < RC; ++a) {
+        const T gl = g * lv[a];
+#pragma unroll
+        for (int b = 0; b < RC; ++b) acc[a * RC + b] = fma(gl, rv[b], acc[a * RC + b]);
+      }
+    }
+  }
+  s2 = warp_sum(s2);
+  if (lane == 0) out[0] = s2;
+  store_partials<T, NV, KIND, RC>(acc, lane, out, P.r[k], P.r[k + 1]);
+}
+
+// Any other chunk: interfaces through tables and chains of core slices, with
+// loops that stop at the runtime ranks.
+template <typename T, int R, int RC>
+__device__ __forceinline__ void warp_chunk_general(const DevProb& P, int k, int beg, int end, const T* Ts, T* out) {
+  const int lane = threadIdx.x & 31;
+  const int ra = P.r[k], rb = P.r[k + 1];
+  constexpr int NV = pow2_at_least(RC * RC);
+  T acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) acc[i] = 0;
+  T s2 = 0;
+  const bool keep = P.keep_residual && k == 0;
+  int e = beg + lane;
+  Code nxt_words = {0u, 0u, 0u, 0u};
+  T nxt_y = 0;
+  if (e < end) {
+    nxt_words = load_code(P, k, e);
+    nxt_y = yval<T>(P, k, e);
+  }
+  for (; e < end; e += 32) {
+    const Code words = nxt_words;
+    const T yv = nxt_y;
+    if (e + 32 < end) {
+      nxt_words = load_code(P, k, e + 32);
+      nxt_y = yval<T>(P, k, e + 32);
+    }
+    T lv[RC], rv[RC];
+    const T g = interfaces<T, R, RC>(P, k, words, Ts, lv, rv) - yv;
+    if (keep) P.g[P.perm[0][e]] = (double)g;
+    s2 = fma(g, g, s2);
+#pragma unroll
+    for (int a = 0; a < RC; ++a) {
+      if (a >= ra) break;
+      const T gl = g * lv[a];
+#pragma unroll
+      for (int b = 0; b < RC; ++b) {
+        if (b >= rb) break;
+        acc[a * RC + b] = fma(gl, rv[b], acc[a * RC + b]);
+      }
+    }
+  }
+  s2 = warp_sum(s2);
+  if (lane == 0) out[0] = s2;
+  store_partials<T, NV, 2, RC>(acc, lane, out, ra, rb);
+}
+
+// Small ranks (R <= 8): one warp reduces one chunk of at most TTC_CHUNK
+// entries of one mode-k slice x.  Each lane takes every 32nd entry (the next
+// entry's code and observation are fetched while the current one is
+// processed), forms its interfaces and residual, and accumulates the
+// rank-one terms g * l_{k-1} r_{k+1}^T and g^2 in registers; a butterfly then
+// sums the lanes.  No shared memory beyond the slice, no block barriers.
+template <typename T, int R, int RC>
+__device__ __forceinline__ void sample_project_warp(const DevProb& P, const int call, T* Ts) {
+  int k = 0;
+  while (k + 1 < P.m && call >= P.chunk_base[k + 1]) ++k;
+  const int c = call - P.chunk_base[k];
+  const int x = P.cseg[k][c];
+  const int beg = P.seg[k][x] + (c - P.cfirst[k][x]) * TTC_CHUNK;
+  const int end = min(beg + TTC_CHUNK, P.seg[k][x + 1]);
+  const int ra = P.r[k], rb = P.r[k + 1];
+  const int lane = threadIdx.x & 31;
+  {
+    const T* S = core_ptr<T>(P, k) + (long long)x * R * R;
+    for (int i = lane; i < R * R; i += 32) {
+      const int a = i / R, b = i % R;
+      Ts[i] = (a < ra && b < rb) ? S[pad_idx(P, k, a, b)] : T(0);
+    }
+  }
+  __syncwarp();
+  T* out = reinterpret_cast<T*>(P.part) + (long long)(P.chunk_base[k] + c) * P.part_stride;
+  RowSrc<T> ls{}, rs{};
+  const bool lrow = (k == 0) || left_src<T>(P, k, ls);
+  const bool rrow = (k == P.m - 1) || right_src<T>(P, k, rs);
+  if (lrow && rrow) {
+    if (k == 0)
+      warp_chunk_rows<T, R, RC, 0>(P, k, beg, end, Ts, ls, rs, out);
+    else if (k == P.m - 1)
+      warp_chunk_rows<T, R, RC, 1>(P, k, beg, end, Ts, ls, rs, out);
+    else
+      warp_chunk_rows<T, R, RC, 2>(P, k, beg, end, Ts, ls, rs, out);
+  } else {
+    warp_chunk_general<T, R, RC>(P, k, beg, end, Ts, out);
+  }
+}
+
+// Large ranks (R >= 16): one block reduces one chunk.  The rank-one terms of
+// 256 entries at a time are staged in shared memory and every thread owns a
+// tile of the r_k x r_{k+1} output.
+template <typename T, int R>
+__device__ __forceinline__ void sample_project_block(const DevProb& P, const int blk) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Ts = reinterpret_cast<T*>(smraw);   // R*R: the pass's own slice
+  T* Lg = Ts + R * R;                     // [TTC_NT][R]
+  T* Rv = Lg + TTC_NT * R;                // [TTC_NT][R]
+
+  int k = 0;
+  while (k + 1 < P.m && blk >= P.chunk_base[k + 1]) ++k;
+  const int c = blk - P.chunk_base[k];
+  const int x = P.cseg[k][c];
+  const int beg = P.seg[k][x] + (c - P.cfirst[k][x]) * TTC_CHUNK;
+  const int end = min(beg + TTC_CHUNK, P.seg[k][x + 1]);
+  const int ra = P.r[k], rb = P.r[k + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  {
+    const T* S = core_ptr<T>(P, k) + (long long)x * R * R;
+    for (int i = tid; i < R * R; i += TTC_NT) {
+      int a = i / R, b = i - (i / R) * R;
+      Ts[i] = (a < ra && b < rb) ? S[pad_idx(P, k, a, b)] : T(0);
+    }
+  }
+  __syncthreads();
+  T* out = reinterpret_cast<T*>(P.part) + (long long)(P.chunk_base[k] + c) * P.part_stride;
+  // output tiles: R == 16 -> one element per thread, R == 32 -> 2 x 2
+  constexpr int TA = (R == 32) ? 2 : 1;
+  constexpr int TB = (R == 32) ? 2 : 1;
+  const int a0 = (tid / (R / TB)) * TA, b0 = (tid % (R / TB)) * TB;
+  T acc[TA][TB];
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int j = 0; j < TB; ++j) acc[i][j] = 0;
+  T s2 = 0;
+  for (int it = 0; it < kEPT; ++it) {
+    const int e = beg + it * TTC_NT + tid;
+    T lv[R], rv[R];
+    T g = 0;
+    if (e < end) {
+      const Code words = load_code(P, k, e);
+      T v = interfaces<T, R, R>(P, k, words, Ts, lv, rv);
+      g = v - yval<T>(P, k, e);
+      if (P.keep_residual && k == 0) P.g[P.perm[0][e]] = (double)g;
+    } else {
+      zero(lv);
+      zero(rv);
+    }
+    s2 = fma(g, g, s2);
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      Lg[tid * R + a] = g * lv[a];
+      Rv[tid * R + a] = rv[a];
+    }
+    __syncthreads();
+    const int cnt = min(TTC_NT, max(0, end - (beg + it * TTC_NT)));
+    for (int t = 0; t < cnt; ++t) {
+      T la[TA], rbv[TB];
+#pragma unroll
+      for (int i = 0; i < TA; ++i) la[i] = Lg[t * R + a0 + i];
+#pragma unroll
+      for (int j = 0; j < TB; ++j) rbv[j] = Rv[t * R + b0 + j];
+#pragma unroll
+      for (int i = 0; i < TA; ++i)
+#pragma unroll
+        for (int j = 0; j < TB; ++j) acc[i][j] = fma(la[i], rbv[j], acc[i][j]);
+    }
+  }
+  T v = warp_sum(s2);
+  __syncthreads();
+  if (lane == 0) Lg[warp] = v;
+  __syncthreads();
+  if (tid == 0) {
+    T tot = 0;
+    for (int w = 0; w < TTC_NT / 32; ++w) tot += Lg[w];
+    out[0] = tot;
+  }
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int j = 0; j < TB; ++j) {
+      const int a = a0 + i, b = b0 + j;
+      if (a < ra && b < rb) out[1 + a * rb + b] = acc[i][j];
+    }
+}
+
+template <typename T, int R, int RC>
+__device__ __forceinline__ void sample_project(const DevProb& P, const int blk) {
+  if constexpr (R <= 8) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int warp = threadIdx.x >> 5;
+    const int call = blk * kWarps + warp;
+    if (call >= P.chunk_base[P.m]) return;
+    sample_project_warp<T, R, RC>(P, call, reinterpret_cast<T*>(smraw) + warp * R * R);
+  } else {
+    sample_project_block<T, R>(P, blk);
+  }
+}
+
+// resident blocks per SM the register budget is sized for: small FP32 ranks
+// keep three 256-thread blocks (24 warps) to cover the gather latency
+template <typename T, int RC>
+constexpr int min_blocks() {
+  return (sizeof(T) == 4 && RC <= 5) ? 3 : 1;
+}
+
+template <typename T, int R, int RC>
+__global__ void __launch_bounds__(TTC_NT, (min_blocks<T, RC>())) k_sample_project(const DevProb P) {
+  sample_project<T, R, RC>(P, blockIdx.x);
+}
+
+// batched form: one launch covers every problem of a batch; blocks
+// [base[p], base[p+1]) belong to problem p
+__device__ __forceinline__ int find_problem(const int* __restrict__ base, int nprob, int blk) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(base + mid) <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// copies a problem descriptor into shared memory (8-byte words)
+__device__ __forceinline__ void stage_desc(const DevProb* __restrict__ src, DevProb* dst) {
+  static_assert(sizeof(DevProb) % 8 == 0, "descriptor size");
+  const uint2* s = reinterpret_cast<const uint2*>(src);
+  uint2* d = reinterpret_cast<uint2*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(DevProb) / 8); i += blockDim.x) d[i] = __ldg(s + i);
+  __syncthreads();
+}
+
+template <typename T, int R, int RC>
+__global__ void __launch_bounds__(TTC_NT, (min_blocks<T, RC>())) k_sample_project_batch(const DevProb* __restrict__ probs,
+                                                                  const int* __restrict__ base, int nprob) {
+  __shared__ __align__(16) DevProb Ps;
+  const int p = find_problem(base, nprob, blockIdx.x);
+  stage_desc(probs + p, &Ps);
+  sample_project<T, R, RC>(Ps, blockIdx.x - __ldg(base + p));
+}
+
+template <typename T>
+inline size_t pass_smem(int R) {
+  if (R <= 8) return sizeof(T) * (size_t)(kWarps * R * R);
+  return sizeof(T) * (size_t)(R * R + 2 * TTC_NT * R);
+}
+
+// one launch of the pass kernel: a single problem (g == nullptr) or a batch group
+template <typename T, int R, int RC>
+int launch(const PassLaunch& L) {
+  const size_t smem = pass_smem<T>(R);
+  if (L.g)
+    k_sample_project_batch<T, R, RC><<<L.g->pass_blocks, TTC_NT, smem, L.st>>>(L.g->probs, L.g->pass_base,
+                                                                                 L.g->nprob);
+  else
+    k_sample_project<T, R, RC><<<ttc_pass_blocks(*L.P, R), TTC_NT, smem, L.st>>>(*L.P);
+  TTC_CUDA(cudaGetLastError());
+  return TTC_OK;
+}
+
+template <typename T, int R, int RC>
+int opt_in() {
+  const size_t smem = pass_smem<T>(R);
+  if (smem > 48 * 1024) {
+    TTC_CUDA(cudaFuncSetAttribute(k_sample_project<T, R, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    TTC_CUDA(cudaFuncSetAttribute(k_sample_project_batch<T, R, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  }
+  return TTC_OK;
+}
+
+}  // namespace ttc_pass

@@ -49,33 +49,70 @@ __device__ __forceinline__ float* tab_ptr<float>(const DevProb& P) { return P.ta
 template <>
 __device__ __forceinline__ double* tab_ptr<double>(const DevProb& P) { return P.tab64; }
 
-// 16-byte loads of the first min(len, RC) entries of a zero-padded row whose
-// storage is padded to a multiple of 4 floats / 2 doubles at least RC long
-// (so every vector read stays inside the row).  Entries from len on are left
-// as they are: callers pass zero-initialised arrays.  Global rows go through
-// the read-only path, shared rows are read directly.
+// 32-byte read-only global loads (sm_100 and later); the address must be
+// 32-byte aligned
+__device__ __forceinline__ void ldg32B(const float* p, float (&v)[8]) {
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+__device__ __forceinline__ void ldg32B(const double* p, double (&v)[4]) {
+  asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+               : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+               : "l"(p));
+}
+
+// Loads the first min(len, RC) entries of a zero-padded row in vectors:
+// 32 bytes at a time from global memory where the row's padded storage
+// holds them (RC above 4 floats / 2 doubles: rows are then padded to 8
+// floats / 4 doubles and 32-byte aligned), else 16 bytes.  Entries from len
+// on are left as they are: callers pass zero-initialised arrays.
 template <int RC, bool kGlobal>
 __device__ __forceinline__ void load_row(const float* __restrict__ row, int len, float (&out)[RC]) {
+  if constexpr (kGlobal && RC > 4) {
 #pragma unroll
-  for (int b = 0; b < RC; b += 4) {
-    if (b >= len) break;
-    const float4 v = kGlobal ? __ldg(reinterpret_cast<const float4*>(row + b))
-                             : *reinterpret_cast<const float4*>(row + b);
-    out[b] = v.x;
-    if (b + 1 < RC) out[b + 1] = v.y;
-    if (b + 2 < RC) out[b + 2] = v.z;
-    if (b + 3 < RC) out[b + 3] = v.w;
+    for (int b = 0; b < RC; b += 8) {
+      if (b >= len) break;
+      float v[8];
+      ldg32B(row + b, v);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (b + i < RC) out[b + i] = v[i];
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < RC; b += 4) {
+      if (b >= len) break;
+      const float4 v = kGlobal ? __ldg(reinterpret_cast<const float4*>(row + b))
+                               : *reinterpret_cast<const float4*>(row + b);
+      out[b] = v.x;
+      if (b + 1 < RC) out[b + 1] = v.y;
+      if (b + 2 < RC) out[b + 2] = v.z;
+      if (b + 3 < RC) out[b + 3] = v.w;
+    }
   }
 }
 template <int RC, bool kGlobal>
 __device__ __forceinline__ void load_row(const double* __restrict__ row, int len, double (&out)[RC]) {
+  if constexpr (kGlobal && RC > 2) {
 #pragma unroll
-  for (int b = 0; b < RC; b += 2) {
-    if (b >= len) break;
-    const double2 v = kGlobal ? __ldg(reinterpret_cast<const double2*>(row + b))
-                              : *reinterpret_cast<const double2*>(row + b);
-    out[b] = v.x;
-    if (b + 1 < RC) out[b + 1] = v.y;
+    for (int b = 0; b < RC; b += 4) {
+      if (b >= len) break;
+      double v[4];
+      ldg32B(row + b, v);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (b + i < RC) out[b + i] = v[i];
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < RC; b += 2) {
+      if (b >= len) break;
+      const double2 v = kGlobal ? __ldg(reinterpret_cast<const double2*>(row + b))
+                                : *reinterpret_cast<const double2*>(row + b);
+      out[b] = v.x;
+      if (b + 1 < RC) out[b + 1] = v.y;
+    }
   }
 }
 

@@ -362,14 +362,41 @@ __device__ __forceinline__ bool right_src(const DevProb& P, int k, RowSrc<T>& s)
   return false;
 }
 
+template <typename T>
+__device__ __forceinline__ const T* y_ptr(const DevProb& P, int k);
+template <>
+__device__ __forceinline__ const float* y_ptr<float>(const DevProb& P, int k) { return P.y32[k]; }
+template <>
+__device__ __forceinline__ const double* y_ptr<double>(const DevProb& P, int k) { return P.y64[k]; }
+
+__device__ __forceinline__ Code load_code_at(const uint32_t* __restrict__ p, int W, int e) {
+  Code c;
+  p += (long long)e * W;
+  c.w0 = __ldg(p);
+  c.w1 = W > 1 ? __ldg(p + 1) : 0u;
+  c.w2 = W > 2 ? __ldg(p + 2) : 0u;
+  c.w3 = W > 3 ? __ldg(p + 3) : 0u;
+  return c;
+}
+
 // One chunk whose interfaces are each one row (or the identity at the ends
 // of the train).  Loops run over the full register size RC: rows, slices and
 // tables are zero-padded, so the extra terms add exact zeros.
 // KIND 0: first mode (l = 1), KIND 1: last mode (r = 1), KIND 2: interior.
-template <typename T, int R, int RC, int KIND>
+// Every lane takes U entries per iteration (their row gathers in flight
+// together) and fetches the next U codes and observations ahead; a lane
+// without an entry for a slot gathers a valid row and contributes g = 0.
+// The descriptor's loop-invariant fields are read once into registers.
+template <typename T, int R, int RC, int KIND, int U>
 __device__ __forceinline__ void warp_chunk_rows(const DevProb& P, int k, int beg, int end, const T* Ts,
                                                 const RowSrc<T>& ls, const RowSrc<T>& rs, T* out) {
   const int lane = threadIdx.x & 31;
+  const uint32_t* __restrict__ code = P.code[k];
+  const int W = P.W;
+  const T* __restrict__ yk = y_ptr<T>(P, k);
+  const bool keep = P.keep_residual && k == 0;
+  double* __restrict__ gout = P.g;
+  const int* __restrict__ perm0 = P.perm[0];
   constexpr int NV = pow2_at_least(KIND == 2 ? RC * RC : RC);
   T acc[NV];
 #pragma unroll
@@ -382,60 +409,77 @@ __device__ __forceinline__ void warp_chunk_rows(const DevProb& P, int k, int beg
     for (int a = 0; a < RC; ++a) tv[a] = Ts[a * R];
   }
   T s2 = 0;
-  const bool keep = P.keep_residual && k == 0;
-  int e = beg + lane;
-  Code nxt_words = {0u, 0u, 0u, 0u};
-  T nxt_y = 0;
-  if (e < end) {
-    nxt_words = load_code(P, k, e);
-    nxt_y = yval<T>(P, k, e);
-  }
-  for (; e < end; e += 32) {
-    const Code words = nxt_words;
-    const T yv = nxt_y;
-    if (e + 32 < end) {
-      nxt_words = load_code(P, k, e + 32);
-      nxt_y = yval<T>(P, k, e + 32);
+  Code nw[U];
+  T ny[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int eu = beg + lane + 32 * u;
+    nw[u] = {0u, 0u, 0u, 0u};
+    ny[u] = 0;
+    if (eu < end) {
+      nw[u] = load_code_at(code, W, eu);
+      ny[u] = __ldg(yk + eu);
     }
-    T lv[RC], rv[RC];
-    zero(lv);
-    zero(rv);
-    if constexpr (KIND != 0) load_row<RC, true>(row_of(ls, words), RC, lv);
-    if constexpr (KIND != 1) load_row<RC, true>(row_of(rs, words), RC, rv);
-    T v = 0;
-    if constexpr (KIND == 0) {
+  }
+  for (int e = beg + lane; e < end; e += 32 * U) {
+    Code w[U];
+    T yv[U];
 #pragma unroll
-      for (int b = 0; b < RC; ++b) v = fma(tv[b], rv[b], v);
-    } else if constexpr (KIND == 1) {
-#pragma unroll
-      for (int a = 0; a < RC; ++a) v = fma(lv[a], tv[a], v);
-    } else {
-#pragma unroll
-      for (int a = 0; a < RC; ++a) {
-        T row[RC];
-        zero(row);
-        load_row<RC, false>(Ts + a * R, RC, row);
-        T t = 0;
-#pragma unroll
-        for (int b = 0; b < RC; ++b) t = fma(row[b], rv[b], t);
-        v = fma(lv[a], t, v);
+    for (int u = 0; u < U; ++u) {
+      w[u] = nw[u];
+      yv[u] = ny[u];
+      const int en = e + 32 * (U + u);
+      if (en < end) {
+        nw[u] = load_code_at(code, W, en);
+        ny[u] = __ldg(yk + en);
       }
     }
-    const T g = v - yv;
-    if (keep) P.g[P.perm[0][e]] = (double)g;
-    s2 = fma(g, g, s2);
-    if constexpr (KIND == 0) {
+    T lv[U][RC], rv[U][RC];
 #pragma unroll
-      for (int b = 0; b < RC; ++b) acc[b] = fma(g, rv[b], acc[b]);
-    } else if constexpr (KIND == 1) {
+    for (int u = 0; u < U; ++u) {
+      zero(lv[u]);
+      zero(rv[u]);
+      if constexpr (KIND != 0) load_row<RC, true>(row_of(ls, w[u]), RC, lv[u]);
+      if constexpr (KIND != 1) load_row<RC, true>(row_of(rs, w[u]), RC, rv[u]);
+    }
 #pragma unroll
-      for (int a = 0; a < RC; ++a) acc[a] = fma(g, lv[a], acc[a]);
-    } else {
+    for (int u = 0; u < U; ++u) {
+      T v = 0;
+      if constexpr (KIND == 0) {
 #pragma unroll
-      for (int a = 0; a < RC; ++a) {
-        const T gl = g * lv[a];
+        for (int b = 0; b < RC; ++b) v = fma(tv[b], rv[u][b], v);
+      } else if constexpr (KIND == 1) {
 #pragma unroll
-        for (int b = 0; b < RC; ++b) acc[a * RC + b] = fma(gl, rv[b], acc[a * RC + b]);
+        for (int a = 0; a < RC; ++a) v = fma(lv[u][a], tv[a], v);
+      } else {
+#pragma unroll
+        for (int a = 0; a < RC; ++a) {
+          T row[RC];
+          zero(row);
+          load_row<RC, false>(Ts + a * R, RC, row);
+          T t = 0;
+#pragma unroll
+          for (int b = 0; b < RC; ++b) t = fma(row[b], rv[u][b], t);
+          v = fma(lv[u][a], t, v);
+        }
+      }
+      const int eu = e + 32 * u;
+      const T g = (eu < end) ? v - yv[u] : T(0);
+      if (keep && eu < end) gout[perm0[eu]] = (double)g;
+      s2 = fma(g, g, s2);
+      if constexpr (KIND == 0) {
+#pragma unroll
+        for (int b = 0; b < RC; ++b) acc[b] = fma(g, rv[u][b], acc[b]);
+      } else if constexpr (KIND == 1) {
+#pragma unroll
+        for (int a = 0; a < RC; ++a) acc[a] = fma(g, lv[u][a], acc[a]);
+      } else {
+#pragma unroll
+        for (int a = 0; a < RC; ++a) {
+          const T gl = g * lv[u][a];
+#pragma unroll
+          for (int b = 0; b < RC; ++b) acc[a * RC + b] = fma(gl, rv[u][b], acc[a * RC + b]);
+        }
       }
     }
   }
@@ -518,13 +562,14 @@ __device__ __forceinline__ void sample_project_warp(const DevProb& P, const int 
   RowSrc<T> ls{}, rs{};
   const bool lrow = (k == 0) || left_src<T>(P, k, ls);
   const bool rrow = (k == P.m - 1) || right_src<T>(P, k, rs);
+  constexpr int U = sizeof(T) == 4 ? 2 : 1;   // FP64 is bound by its FMA rate
   if (lrow && rrow) {
     if (k == 0)
-      warp_chunk_rows<T, R, RC, 0>(P, k, beg, end, Ts, ls, rs, out);
+      warp_chunk_rows<T, R, RC, 0, U>(P, k, beg, end, Ts, ls, rs, out);
     else if (k == P.m - 1)
-      warp_chunk_rows<T, R, RC, 1>(P, k, beg, end, Ts, ls, rs, out);
+      warp_chunk_rows<T, R, RC, 1, U>(P, k, beg, end, Ts, ls, rs, out);
     else
-      warp_chunk_rows<T, R, RC, 2>(P, k, beg, end, Ts, ls, rs, out);
+      warp_chunk_rows<T, R, RC, 2, U>(P, k, beg, end, Ts, ls, rs, out);
   } else {
     warp_chunk_general<T, R, RC>(P, k, beg, end, Ts, out);
   }
@@ -633,10 +678,10 @@ __device__ __forceinline__ void sample_project(const DevProb& P, const int blk) 
 }
 
 // resident blocks per SM the register budget is sized for: small FP32 ranks
-// keep three 256-thread blocks (24 warps) to cover the gather latency
+// keep two 256-thread blocks (16 warps, two gathers in flight each)
 template <typename T, int RC>
 constexpr int min_blocks() {
-  return (sizeof(T) == 4 && RC <= 5) ? 3 : 1;
+  return (sizeof(T) == 4 && RC <= 5) ? 2 : 1;
 }
 
 template <typename T, int R, int RC>

@@ -518,6 +518,270 @@ __global__ void __launch_bounds__(kThreads) k_stage(const DevProb P, const Stage
   }
 }
 
+// ---- warp-per-slice forms (ranks <= 8, so q <= 16) --------------------------
+// One warp handles one slice at a time: the slice is staged in the warp's
+// shared scratch, intermediate products are spread over the lanes, and every
+// lane owns NO outputs of the r x r (or q x q) result, accumulated in
+// registers over the warp's slices with NO independent FMA chains (FP64 has a
+// long dependent latency here).  The eight warps of a block are then summed in
+// warp order, so results stay reproducible.
+
+constexpr int kWarpsW = kThreads / 32;
+constexpr int kWScr = 3 * 16 * 16;   // doubles of scratch per warp
+
+// Y (M x N, ld N) = X (M x K, ld ldx) Z (K x N, ld ldz), spread over the lanes
+__device__ __forceinline__ void warp_mm(double* Y, const double* X, int ldx, const double* Z, int ldz, int M, int N,
+                                        int K, double alpha) {
+  const int lane = threadIdx.x & 31;
+  for (int e = lane; e < M * N; e += 32) {
+    const int i = e / N, j = e - (e / N) * N;
+    double acc = 0.0;
+    for (int t = 0; t < K; ++t) acc = fma(X[i * ldx + t], Z[t * ldz + j], acc);
+    Y[e] = alpha * acc;
+  }
+  __syncwarp();
+}
+
+// warp copy of n contiguous doubles
+__device__ __forceinline__ void warp_load(double* dst, const double* src, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < n; i += 32) dst[i] = src[i];
+  __syncwarp();
+}
+
+// acc[t] += w sum_i L[i*ldl + ia[t]] R[i*ldr + ib[t]]   (columns against columns)
+template <int NO>
+__device__ __forceinline__ void acc_cols(double (&acc)[NO], const int (&ia)[NO], const int (&ib)[NO], const double* L,
+                                         int ldl, const double* R, int ldr, int K, double w) {
+  double t[NO];
+#pragma unroll
+  for (int u = 0; u < NO; ++u) t[u] = 0.0;
+  for (int i = 0; i < K; ++i) {
+#pragma unroll
+    for (int u = 0; u < NO; ++u) t[u] = fma(L[i * ldl + ia[u]], R[i * ldr + ib[u]], t[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < NO; ++u) acc[u] = fma(w, t[u], acc[u]);
+}
+// acc[t] += w sum_i L[ia[t]*ldl + i] R[ib[t]*ldr + i]   (rows against rows)
+template <int NO>
+__device__ __forceinline__ void acc_rows(double (&acc)[NO], const int (&ia)[NO], const int (&ib)[NO], const double* L,
+                                         int ldl, const double* R, int ldr, int K, double w) {
+  double t[NO];
+#pragma unroll
+  for (int u = 0; u < NO; ++u) t[u] = 0.0;
+  for (int i = 0; i < K; ++i) {
+#pragma unroll
+    for (int u = 0; u < NO; ++u) t[u] = fma(L[ia[u] * ldl + i], R[ib[u] * ldr + i], t[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < NO; ++u) acc[u] = fma(w, t[u], acc[u]);
+}
+
+// the contribution of slice x to job J (same sums as slice_contrib)
+template <int NO>
+__device__ void warp_contrib(const DevProb& P, const Job& J, int x, double (&acc)[NO], const int (&ia)[NO],
+                             const int (&ib)[NO], double* scr) {
+  const int k = J.k;
+  const int ra = P.r[k], rb = P.r[k + 1];
+  double* A = scr;
+  double* Y = scr + 256;
+  switch (J.op) {
+    case OP_LAM: {   // acc += w2 T^T (Lam T)
+      warp_load(A, P.core64[k] + (long long)x * ra * rb, ra * rb);
+      warp_mm(Y, P.small + P.off_lam[k], ra, A, rb, ra, rb, ra, 1.0);
+      acc_cols<NO>(acc, ia, ib, A, rb, Y, rb, ra, gpow(P, k, x, +1));
+      break;
+    }
+    case OP_GAM: {   // acc += w2 (T Gam) T^T
+      warp_load(A, P.core64[k] + (long long)x * ra * rb, ra * rb);
+      warp_mm(Y, A, rb, P.small + P.off_gam[k + 1], rb, ra, rb, rb, 1.0);
+      acc_rows<NO>(acc, ia, ib, Y, rb, A, rb, rb, gpow(P, k, x, +1));
+      break;
+    }
+    case OP_H: {     // acc += T^T E
+      warp_load(A, P.core64[k] + (long long)x * ra * rb, ra * rb);
+      warp_load(Y, P.E[k] + (long long)x * ra * rb, ra * rb);
+      acc_cols<NO>(acc, ia, ib, A, rb, Y, rb, ra, 1.0);
+      break;
+    }
+    case OP_PSI: {   // acc += (C Psi) C^T
+      const int qa = P.q[k], qb = P.q[k + 1];
+      warp_load(A, P.C[k] + (long long)x * qa * qb, qa * qb);
+      warp_mm(Y, A, qb, P.small + P.off_psi[k + 1], qb, qa, qb, qb, 1.0);
+      acc_rows<NO>(acc, ia, ib, Y, qb, A, qb, qb, 1.0);
+      break;
+    }
+    default: {       // OP_N: C' = S_{k-1} C ; acc += C'^T C'
+      const int qa = P.q[k], qb = P.q[k + 1];
+      warp_load(A, P.C[k] + (long long)x * qa * qb, qa * qb);
+      if (k == 0) {
+        acc_cols<NO>(acc, ia, ib, A, qb, A, qb, qa, 1.0);
+      } else {
+        warp_mm(Y, P.small + P.off_sk[k - 1], qa, A, qb, ra, qb, qa, 1.0);
+        acc_cols<NO>(acc, ia, ib, Y, qb, Y, qb, ra, 1.0);
+      }
+      break;
+    }
+  }
+  __syncwarp();
+}
+
+// new core k at slice x from C'_k = S_{k-1} C_k (same as slice_map)
+__device__ void warp_slice_map(const DevProb& P, int k, int x, double* scr) {
+  const int lane = threadIdx.x & 31;
+  const int m = P.m;
+  const int qa = P.q[k], qb = P.q[k + 1];
+  const int ra = P.r[k], rb = P.r[k + 1];
+  double* A = scr;
+  double* Y = scr + 256;
+  double* Z = scr + 512;
+  warp_load(A, P.C[k] + (long long)x * qa * qb, qa * qb);
+  const double* Cp = A;
+  if (k > 0) {
+    warp_mm(Y, P.small + P.off_sk[k - 1], qa, A, qb, ra, qb, qa, 1.0);
+    Cp = Y;
+  }
+  const double* Tn = Cp;
+  if (k < m - 1) {
+    warp_mm(Z, Cp, qb, P.small + P.off_pk[k], rb, ra, rb, qb, 1.0);
+    Tn = Z;
+  }
+  double* T = P.core64[k] + (long long)x * ra * rb;
+  float* T32 = P.core32p[k] + (long long)x * P.R * P.R;
+  double* T64 = P.core64p[k] + (long long)x * P.R * P.R;
+  for (int i = lane; i < ra * rb; i += 32) {
+    const int a = i / rb, b = i - (i / rb) * rb;
+    const double v = Tn[i];
+    T[i] = v;
+    T32[pad_idx(P, k, a, b)] = (float)v;
+    T64[pad_idx(P, k, a, b)] = v;
+  }
+  __syncwarp();
+}
+
+template <int NO>
+__global__ void __launch_bounds__(kThreads) k_stage_w(const DevProb P, const Stage S) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ int am_last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* scr = sm + warp * kWScr;
+  int b = blockIdx.x;
+  for (int i = 0; i < S.nmap; ++i) {     // slice maps first, one slice per warp
+    const int k = S.map_k[i];
+    const int nbm = (P.n[k] + kWarpsW - 1) / kWarpsW;
+    if (b < nbm) {
+      const int x = b * kWarpsW + warp;
+      if (x < P.n[k]) warp_slice_map(P, k, x, scr);
+      return;
+    }
+    b -= nbm;
+  }
+  int j = 0;
+  while (b >= S.job[j].nb) {
+    b -= S.job[j].nb;
+    ++j;
+  }
+  const Job J = S.job[j];
+  const int dd = J.rows * J.cols;
+  double acc[NO];
+  int ia[NO], ib[NO];
+#pragma unroll
+  for (int u = 0; u < NO; ++u) {
+    acc[u] = 0.0;
+    const int o = min(lane + 32 * u, dd - 1);
+    ia[u] = o / J.cols;
+    ib[u] = o - ia[u] * J.cols;
+  }
+  const int stride = J.nb * kWarpsW;
+  for (int x = b * kWarpsW + warp; x < P.n[J.k]; x += stride) warp_contrib<NO>(P, J, x, acc, ia, ib, scr);
+  __syncthreads();                       // the scratch becomes the warp-sum area
+#pragma unroll
+  for (int u = 0; u < NO; ++u) {
+    const int o = lane + 32 * u;
+    if (o < dd) sm[warp * dd + o] = acc[u];
+  }
+  __syncthreads();
+  double* out = P.red + J.red + (long long)b * dd;
+  for (int o = threadIdx.x; o < dd; o += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < kWarpsW; ++w) t += sm[w * dd + o];
+    out[o] = t;
+  }
+  // the last reduction block finishes the stage
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int total = 0;
+    for (int t = 0; t < S.njob; ++t) total += S.job[t].nb;
+    int prev = atomicAdd(P.counters + S.counter, 1);
+    am_last = (prev == total - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  for (int t = 0; t < S.njob; ++t) finish_job(P, S.job[t], sm);
+  if (threadIdx.x == 0) P.counters[S.counter] = 0;
+  __threadfence_block();
+  __syncthreads();
+  if (S.post == POST_SMALL_PROJ) {
+    post_small_proj(P, sm);
+  } else if (S.post == POST_BOND) {
+    post_bond(P, S.post_k, sm);
+  }
+}
+
+// B_k(x) and the block core C_k(x), one slice per warp (same as k_build_C)
+__global__ void __launch_bounds__(kThreads) k_build_C_w(const DevProb P, int nslices) {
+  extern __shared__ __align__(16) double sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* scr = sm + warp * kWScr;
+  int g = blockIdx.x * kWarpsW + warp;
+  if (g >= nslices) return;
+  int k = 0;
+  while (k < P.m - 1 && g >= P.n[k]) {
+    g -= P.n[k];
+    ++k;
+  }
+  const int x = g, m = P.m;
+  const int ra = P.r[k], rb = P.r[k + 1];
+  const double alpha = P.scal[SC_ALPHA];
+  const double wi = gpow(P, k, x, -1);
+  double* Tt = scr;
+  double* t1 = scr + 256;
+  double* B = scr + 512;
+  warp_load(Tt, P.core64[k] + (long long)x * ra * rb, ra * rb);
+  warp_mm(t1, P.small + P.off_lami[k], ra, P.E[k] + (long long)x * ra * rb, rb, ra, rb, ra, 1.0);
+  warp_mm(B, t1, rb, P.small + P.off_gami[k + 1], rb, ra, rb, rb, -alpha * wi);
+  if (k + 1 < m) {
+    const double* Q = P.small + P.off_qm[k];
+    for (int e = lane; e < ra * rb; e += 32) {
+      const int i = e / rb, j = e - (e / rb) * rb;
+      double acc = 0.0;
+      for (int t = 0; t < rb; ++t) acc = fma(Tt[i * rb + t], Q[t * rb + j], acc);
+      B[e] = fma(alpha, acc, B[e]);
+    }
+    __syncwarp();
+  }
+  const int qa = P.q[k], qb = P.q[k + 1];
+  double* C = P.C[k] + (long long)x * qa * qb;
+  for (int i = lane; i < qa * qb; i += 32) {
+    int a = i / qb, b = i - (i / qb) * qb;
+    double v;
+    if (k == 0) {
+      v = (b < rb) ? B[a * rb + b] : Tt[a * rb + (b - rb)];
+    } else if (k == m - 1) {
+      v = (a < ra) ? Tt[a * rb + b] : Tt[(a - ra) * rb + b] + B[(a - ra) * rb + b];
+    } else {
+      if (a < ra)
+        v = (b < rb) ? Tt[a * rb + b] : 0.0;
+      else
+        v = (b < rb) ? B[(a - ra) * rb + b] : Tt[(a - ra) * rb + (b - rb)];
+    }
+    C[i] = v;
+  }
+}
+
 // one block per slice (k, x): B_k(x) and the block core C_k(x)
 __global__ void __launch_bounds__(128) k_build_C(const DevProb P) {
   __shared__ double t1[TTC_MAXR * TTC_MAXR];
@@ -655,6 +919,8 @@ struct Plan {
   std::vector<Stage> sweep;      // bond k (+ map of core k-1), then the final maps
   std::vector<Stage> metric[2];  // Gram sweep of ||A - B||^2, which = 0 truth, 1 previous
   size_t smem_stage = 0;
+  bool warp = false;          // warp-per-slice kernels (ranks <= 8)
+  size_t smem_warp = 0;
   double* metric_part = nullptr;
 };
 
@@ -667,6 +933,7 @@ Plan& plan_of(const ttc_ctx* c) {
 }
 
 inline int nblocks_for(int nk) { return std::max(1, std::min(nk, 1024)); }
+inline int nblocks_warp(int nk) { return std::max(1, std::min((nk + kWarpsW - 1) / kWarpsW, 256)); }
 
 int launch_stage(ttc_ctx* c, const Stage& S, size_t smem) {
   int nb = 0;
@@ -676,6 +943,34 @@ int launch_stage(ttc_ctx* c, const Stage& S, size_t smem) {
   TTC_CUDA(cudaGetLastError());
   c->nlaunch += 1;
   return TTC_OK;
+}
+
+// warp-per-slice stage: NO outputs per lane for the largest job of the stage
+int launch_stage_w(ttc_ctx* c, const Stage& S, size_t smem) {
+  int nb = 0, dd = 1;
+  for (int i = 0; i < S.nmap; ++i) nb += (int)((c->n[S.map_k[i]] + kWarpsW - 1) / kWarpsW);
+  for (int j = 0; j < S.njob; ++j) {
+    nb += S.job[j].nb;
+    dd = std::max(dd, S.job[j].rows * S.job[j].cols);
+  }
+  const int no = (dd + 31) / 32;
+  if (no <= 1)
+    k_stage_w<1><<<nb, kThreads, smem, c->stream>>>(c->hp, S);
+  else if (no <= 2)
+    k_stage_w<2><<<nb, kThreads, smem, c->stream>>>(c->hp, S);
+  else if (no <= 4)
+    k_stage_w<4><<<nb, kThreads, smem, c->stream>>>(c->hp, S);
+  else if (no <= 8)
+    k_stage_w<8><<<nb, kThreads, smem, c->stream>>>(c->hp, S);
+  else
+    return TTC_EUNSUPPORTED;
+  TTC_CUDA(cudaGetLastError());
+  c->nlaunch += 1;
+  return TTC_OK;
+}
+
+int run_stage(ttc_ctx* c, const Plan& pl, const Stage& S) {
+  return pl.warp ? launch_stage_w(c, S, pl.smem_warp) : launch_stage(c, S, pl.smem_stage);
 }
 
 }  // namespace
@@ -737,13 +1032,19 @@ int ttc_alloc_dense(ttc_ctx* c) {
   P.counters = counters;
 
   Plan pl;
+  {
+    int qm = 1;
+    for (int k = 0; k <= m; ++k) qm = std::max(qm, P.q[k]);
+    pl.warp = qm <= 16;
+  }
   long long red = 0;
   int ctr = 1;   // counter 0 belongs to the slice reduction of the sampled pass
+  bool warp_jobs = pl.warp;   // the metric stages below always use the block kernel
   auto mk = [&](int op, int k, int rows, int cols, int dst) {
     Job J;
     J.op = op;
     J.k = k;
-    J.nb = nblocks_for((int)c->n[k]);
+    J.nb = warp_jobs ? nblocks_warp((int)c->n[k]) : nblocks_for((int)c->n[k]);
     J.rows = rows;
     J.cols = cols;
     J.red = red;
@@ -790,6 +1091,7 @@ int ttc_alloc_dense(ttc_ctx* c) {
     S.map_k[S.nmap++] = m - 1;
     pl.sweep.push_back(S);
   }
+  warp_jobs = false;
   for (int which = 0; which < 2; ++which) {
     for (int k = 0; k < m; ++k) {
       Stage S = blank();
@@ -821,6 +1123,7 @@ int ttc_alloc_dense(ttc_ctx* c) {
   size_t bond_need = sizeof(double) * (size_t)(2 * qmax * qmax + 5 * qmax * rmax + 6 * rmax * rmax + kThreads) +
                      sizeof(float) * (size_t)(2 * rmax * rmax);
   pl.smem_stage = std::max(red_need, std::max(proj_need, bond_need)) + 64;
+  pl.smem_warp = std::max(pl.smem_stage, sizeof(double) * (size_t)kWarpsW * kWScr);
   {
     // the attribute is per device and shared by every context: only raise it,
     // so that contexts needing more than this one keep launching
@@ -829,9 +1132,15 @@ int ttc_alloc_dense(ttc_ctx* c) {
     std::lock_guard<std::mutex> lk(mu);
     int dev = 0;
     TTC_CUDA(cudaGetDevice(&dev));
-    if (granted[dev] < pl.smem_stage) {
-      TTC_CUDA(cudaFuncSetAttribute(k_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem_stage));
-      granted[dev] = pl.smem_stage;
+    if (granted[dev] < pl.smem_warp) {
+      const int sz = (int)pl.smem_warp;   // >= smem_stage
+      TTC_CUDA(cudaFuncSetAttribute(k_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+      TTC_CUDA(cudaFuncSetAttribute(k_stage_w<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+      TTC_CUDA(cudaFuncSetAttribute(k_stage_w<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+      TTC_CUDA(cudaFuncSetAttribute(k_stage_w<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+      TTC_CUDA(cudaFuncSetAttribute(k_stage_w<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+      TTC_CUDA(cudaFuncSetAttribute(k_build_C_w, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+      granted[dev] = pl.smem_warp;
     }
   }
   plan_of(c) = pl;
@@ -843,14 +1152,17 @@ int ttc_launch_dense(ttc_ctx* c) {
   const int m = c->m;
   Plan& pl = plan_of(c);
   cudaStream_t st = c->stream;
-  for (auto& S : pl.gram) TTC_TRY(launch_stage(c, S, pl.smem_stage));
+  for (auto& S : pl.gram) TTC_TRY(run_stage(c, pl, S));
   int nslices = 0;
   for (int k = 0; k < m; ++k) nslices += (int)c->n[k];
-  k_build_C<<<nslices, 128, 0, st>>>(P);
+  if (pl.warp)
+    k_build_C_w<<<(nslices + kWarpsW - 1) / kWarpsW, kThreads, sizeof(double) * kWarpsW * kWScr, st>>>(P, nslices);
+  else
+    k_build_C<<<nslices, 128, 0, st>>>(P);
   TTC_CUDA(cudaGetLastError());
   c->nlaunch += 1;
-  for (auto& S : pl.psi) TTC_TRY(launch_stage(c, S, pl.smem_stage));
-  for (auto& S : pl.sweep) TTC_TRY(launch_stage(c, S, pl.smem_stage));
+  for (auto& S : pl.psi) TTC_TRY(run_stage(c, pl, S));
+  for (auto& S : pl.sweep) TTC_TRY(run_stage(c, pl, S));
   return TTC_OK;
 }
 

@@ -70,9 +70,7 @@ int build_groups(ttc_batch* b) {
       G.idx.push_back(i);
       descs.push_back(c->hp);
       pb.push_back(pb.back() + ttc_pass_blocks(c->hp, key.second));
-      int nseg = 0;
-      for (int k = 0; k < c->m; ++k) nseg += c->hp.n[k];
-      sb.push_back(sb.back() + nseg);
+      sb.push_back(sb.back() + ttc_seg_blocks(c->hp));
       tb.push_back(tb.back() + c->hp.tab_total);
     }
     cudaError_t e = cudaMalloc(&G.probs, sizeof(DevProb) * descs.size());

@@ -111,6 +111,13 @@ int ttc_pass_small_f64(int RC, const PassLaunch& L);
 int ttc_pass_large(bool f32, int R, const PassLaunch& L);
 int ttc_pass_opt_in_large();
 
+// blocks of the slice reduction: one slice per warp, 8 per block
+inline int ttc_seg_blocks(const DevProb& P) {
+  int nseg = 0;
+  for (int k = 0; k < P.m; ++k) nseg += P.n[k];
+  return (nseg + 7) / 8;
+}
+
 // omega_pass.cu
 int ttc_launch_omega_pass_batch(const BatchGroup& g, cudaStream_t st, int phase);   // 0: pass, 1: slice reduction, 2: tables
 void ttc_plan_tables(ttc_ctx* c);

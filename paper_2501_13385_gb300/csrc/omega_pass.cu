@@ -12,6 +12,18 @@ namespace {
 
 using namespace ttc_pass;
 
+// 16-byte stores of a padded row (R a multiple of 4)
+template <int R>
+__device__ __forceinline__ void store_row(float* dst, const float (&v)[R]) {
+#pragma unroll
+  for (int b = 0; b < R; b += 4) *reinterpret_cast<float4*>(dst + b) = make_float4(v[b], v[b + 1], v[b + 2], v[b + 3]);
+}
+template <int R>
+__device__ __forceinline__ void store_row(double* dst, const double (&v)[R]) {
+#pragma unroll
+  for (int b = 0; b < R; b += 2) *reinterpret_cast<double2*>(dst + b) = make_double2(v[b], v[b + 1]);
+}
+
 // one table row per thread: the chain of core slices it stands for (rows
 // whose coordinates are outside the mode sizes are written as zeros)
 template <typename T, int R>
@@ -38,9 +50,10 @@ __device__ __forceinline__ void build_table_row(const DevProb& P, long long g) {
       for (int j = last; j >= first; --j) times_col<T, R, R>(P, j, xs[j], v);
   }
   const int len = valid ? P.r[jt] : 0;
-  T* dst = tab_ptr<T>(P) + g * R;
 #pragma unroll
-  for (int a = 0; a < R; ++a) dst[a] = (a < len) ? v[a] : T(0);
+  for (int a = 0; a < R; ++a)
+    if (a >= len) v[a] = T(0);
+  store_row<R>(tab_ptr<T>(P) + g * R, v);
 }
 
 template <typename T, int R>
@@ -67,34 +80,42 @@ __global__ void __launch_bounds__(256) k_build_tables_batch(const DevProb* __res
 
 inline int table_blocks(long long rows) {
   long long b = (rows + 255) / 256;
-  return (int)(b < 4 * 152 ? (b < 1 ? 1 : b) : 4 * 152);
+  return (int)(b < 64 * 152 ? (b < 1 ? 1 : b) : 64 * 152);
 }
 
 
-// sums the chunk partials of every slice (k, x) in chunk order, in FP64; the
-// last block then forms ||G_l||^2 = sum_x s_1(x), eps_l and alpha_l
-// (step-size form of Theorem 4.1; eps reading in the options)
+// sums the chunk partials of every slice (k, x) in chunk order, in FP64, one
+// slice per warp (kSegSlices per block); the last block then forms
+// ||G_l||^2 = sum_x s_1(x), eps_l and alpha_l (step-size form of Theorem 4.1;
+// eps reading in the options)
+constexpr int kSegThreads = 256;
+constexpr int kSegSlices = kSegThreads / 32;
+
 template <typename T>
 __device__ __forceinline__ void segment_reduce_block(const DevProb& P, int blk, int total_blocks) {
   __shared__ int am_last;
-  __shared__ double sh[128];
+  __shared__ double sh[kSegThreads];
+  const int lane = threadIdx.x & 31;
+  int g = blk * kSegSlices + (threadIdx.x >> 5);
   int k = 0;
-  while (k < P.m - 1 && blk >= P.n[k]) {
-    blk -= P.n[k];
+  while (k < P.m - 1 && g >= P.n[k]) {
+    g -= P.n[k];
     ++k;
   }
-  const int x = blk;
-  const int ra = P.r[k], rb = P.r[k + 1];
-  const int nout = 1 + ra * rb;
-  const int c0 = P.cfirst[k][x], c1 = P.cfirst[k][x + 1];
-  const T* part = reinterpret_cast<const T*>(P.part) + (long long)P.chunk_base[k] * P.part_stride;
-  for (int j = threadIdx.x; j < nout; j += blockDim.x) {
-    double acc = 0.0;
-    for (int cc = c0; cc < c1; ++cc) acc += (double)part[(long long)cc * P.part_stride + j];
-    if (j == 0)
-      P.s[k][x] = acc;
-    else
-      P.E[k][(long long)x * ra * rb + (j - 1)] = acc;
+  if (g < P.n[k]) {
+    const int x = g;
+    const int ra = P.r[k], rb = P.r[k + 1];
+    const int nout = 1 + ra * rb;
+    const int c0 = P.cfirst[k][x], c1 = P.cfirst[k][x + 1];
+    const T* part = reinterpret_cast<const T*>(P.part) + (long long)P.chunk_base[k] * P.part_stride;
+    for (int j = lane; j < nout; j += 32) {
+      double acc = 0.0;
+      for (int cc = c0; cc < c1; ++cc) acc += (double)part[(long long)cc * P.part_stride + j];
+      if (j == 0)
+        P.s[k][x] = acc;
+      else
+        P.E[k][(long long)x * ra * rb + (j - 1)] = acc;
+    }
   }
   __threadfence();
   __syncthreads();
@@ -177,9 +198,8 @@ int launch_pass(ttc_ctx* c, int RC) {
   PassLaunch L{&P, nullptr, c->stream};
   TTC_TRY(launch_pass_kernel(sizeof(T) == 4, R, RC, L));
   if (c->prof) TTC_CUDA(cudaEventRecordWithFlags(c->ev_end, c->stream, evflags));
-  int nseg = 0;
-  for (int k = 0; k < P.m; ++k) nseg += P.n[k];
-  k_segment_reduce<T><<<nseg, 128, 0, c->stream>>>(P, nseg);
+  const int nsegb = ttc_seg_blocks(P);
+  k_segment_reduce<T><<<nsegb, kSegThreads, 0, c->stream>>>(P, nsegb);
   TTC_CUDA(cudaGetLastError());
   c->nlaunch += 2;
   return TTC_OK;
@@ -202,7 +222,7 @@ int launch_pass_batch(const BatchGroup& g, cudaStream_t st, int phase) {
     PassLaunch L{nullptr, &g, st};
     return launch_pass_kernel(sizeof(T) == 4, R, g.RC, L);
   } else {
-    k_segment_reduce_batch<T><<<g.seg_blocks, 128, 0, st>>>(g.probs, g.seg_base, g.nprob);
+    k_segment_reduce_batch<T><<<g.seg_blocks, kSegThreads, 0, st>>>(g.probs, g.seg_base, g.nprob);
   }
   TTC_CUDA(cudaGetLastError());
   return TTC_OK;

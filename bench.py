@@ -167,18 +167,63 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def algorithmic_bytes_per_launch(P, W=1, chunk=1024):
+def code_plan(n):
+    """Packed-code layout of the coordinates (fields never straddle a 32-bit
+    word): per mode (word, shift, bits), and the words per entry."""
+    word, shift, plan = 0, 0, []
+    for nk in n:
+        bits = max(0, int(nk - 1).bit_length())
+        if shift + bits > 32:
+            word, shift = word + 1, 0
+        plan.append((word, shift, bits))
+        shift += bits
+    W = word + 1
+    return plan, (4 if W == 3 else W)
+
+
+def table_rows(P, cap_rows):
+    """Valid rows of the interface tables the library keeps (prefix tables
+    over modes 0..j-1, j >= 2, and suffix tables over modes j..d-1, j <= d-2,
+    whose modes share one code word and whose bit-indexed row count stays
+    within the cap)."""
+    import math
+    plan, _ = code_plan(P.n)
+    cap = min(1 << 17, max(4096, 4 * P.N)) if cap_rows is None else cap_rows
+    rows, m = [], P.m
+
+    def ok(first, last):
+        if plan[first][0] != plan[last][0]:
+            return False
+        bits = plan[last][1] + plan[last][2] - plan[first][1]
+        return bits <= 17 and (1 << bits) <= cap
+    for j in range(2, m):
+        if not ok(0, j - 1):
+            break
+        rows.append(math.prod(P.n[:j]))
+    for j in range(m - 2, 0, -1):
+        if not ok(j, m - 1):
+            break
+        rows.append(math.prod(P.n[j:]))
+    return rows
+
+
+def algorithmic_bytes_per_launch(P, chunk=1024):
     """Bytes the sampled pass must move per launch for one problem: for every
-    mode k, every entry's packed code (4W bytes) and FP32 value (4 bytes),
-    plus one FP32 partial (1 + r_k r_{k+1} values) written per chunk of
-    `chunk` entries of a slice.  Core slices are L2/L1-resident and not
-    counted."""
+    mode k, every entry's packed code (4W bytes) and FP32 value (4 bytes), one
+    FP32 partial (1 + r_k r_{k+1} values) written per chunk of `chunk` entries
+    of a slice, and, read once, the valid rows of the interface tables and the
+    padded FP32 core slices (rows of R = rank-bucket floats)."""
     import numpy as np
+    _, W = code_plan(P.n)
+    rmax = max(P.r)
+    R = 4 if rmax <= 4 else 8 if rmax <= 8 else 16 if rmax <= 16 else 32
     total = 0
     for k in range(P.m):
         counts = np.bincount(P.idx[:, k], minlength=P.n[k])
         chunks = int(np.sum((counts + chunk - 1) // chunk))
         total += P.N * (4 * W + 4) + chunks * (1 + P.r[k] * P.r[k + 1]) * 4
+        total += P.n[k] * R * R * 4
+    total += sum(table_rows(P, None)) * R * 4
     return total
 
 
@@ -359,9 +404,11 @@ def ttc_arm(args):
     alg = sum(algorithmic_bytes_per_launch(P) for P in probs)
     kern_avg_ms = kern_ms / max(kern_n, 1)
     achieved = alg / (kern_avg_ms / 1e3) / 1e9
-    traffic = load_traffic(os.path.join(ROOT, "paper_2501_13385_gb300", "csrc", "omega_pass.cu"), B)
+    traffic = load_traffic(os.path.join(ROOT, "paper_2501_13385_gb300", "csrc", "omega_pass.cuh"), B)
+    rmax0 = max(probs[0].r)
+    R_bucket = 4 if rmax0 <= 4 else 8 if rmax0 <= 8 else 16 if rmax0 <= 16 else 32
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": "k_sample_project_batch<float,8>", "kernel_ms": kern_avg_ms,
+            "traffic": traffic, "kernel": f"k_sample_project_batch<float,{R_bucket},{max(probs[0].r)}>", "kernel_ms": kern_avg_ms,
             "launches_timed": kern_n, "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
 
     cpu = None

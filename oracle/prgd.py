@@ -17,7 +17,8 @@ Readings of points the paper leaves open (each is a documented choice):
     (the theory indexes it by l, Theorem 4.1); `eps_mode="frozen"` keeps the
     value of iteration 0.
   * the step size is the constant-in-form choice of Theorem 4.1,
-    alpha_l = alpha_scale * eps_l^{1/2} / p with p = |Omega| / d*.
+    alpha_l = alpha_scale * eps_l^{1/2} / p with p = |Omega| / d*; the
+    steepest step of Eq. (PRGD stepsize) is the "adaptive" variant.
   * the Trim step of Algorithm 2 is skipped, which Section 3.2 allows.
   * the left-orthogonal decomposition of W^{1/2} T is taken by Householder QR
     (any left-orthogonal decomposition spans the same tangent space).
@@ -302,6 +303,44 @@ def assemble_2r(U, A, alpha, G) -> Cores:
     return C
 
 
+def tangent_tt(U, A) -> Cores:
+    """The tangent vector sum_i [U_1, ..., A_i, ..., U_m] (Section 3.3,
+    tangent space parameterisation) as one TT of rank 2r: cores [A_1 U_1],
+    [[U_i, 0], [A_i, U_i]] and [[U_m], [A_m]]."""
+    m = len(U)
+    out = []
+    for i in range(m):
+        Ui, Ai = U[i], A[i]
+        ra, d, rb = Ui.shape
+        if m == 1:
+            c = Ai.copy()
+        elif i == 0:
+            c = np.concatenate([Ai, Ui], axis=2)
+        elif i == m - 1:
+            c = np.concatenate([Ui, Ai], axis=0)
+        else:
+            c = np.zeros((2 * ra, d, 2 * rb))
+            c[:ra, :, :rb] = Ui
+            c[ra:, :, :rb] = Ai
+            c[ra:, :, rb:] = Ui
+        out.append(c)
+    return out
+
+
+def adaptive_step(U, A, G, idx) -> float:
+    """The steepest step along the search direction, Eq. (PRGD stepsize):
+    alpha_l = ||Z||_W^2 / ||P_Omega Z||_F^2 with Z = tilde P_T W^{-1} G_l.
+    By Lemma 3.5, W^{1/2} Z = P_{T^} W^{-1/2} G_l is the tangent TT of the
+    components A at U, so ||Z||_W is its Frobenius norm; Z itself is that TT
+    with every core slice scaled by G_i(x)^{-1/(4m)} (Proposition 3.1),
+    evaluated at Omega."""
+    m = len(U)
+    Zhat = tangent_tt(U, A)
+    num = tt_norm(Zhat) ** 2
+    z = tt_eval(scale_cores(Zhat, G, -1.0 / (4 * m)), idx)
+    return num / float(z @ z)
+
+
 def tt_round(C, r) -> Cores:
     """SVD^tt_r of a TT given by cores (Algorithm 1 applied to a low-rank TT):
     right-to-left Householder QR of R(C_k)^T, then left-to-right truncated SVD
@@ -350,27 +389,44 @@ class StepInfo:
 
 
 def prgd_step(cores, idx, y, n, r, eps_rel=1.0, alpha_scale=1.0, eps=None, alpha=None,
-              keep=False):
+              keep=False, step="constant", metric="precond", retraction="plain"):
     """One PRGD iteration (Algorithm 2, Trim skipped):
     G_l = P_Omega(T_l - T*); G_{l,i}; W_l = T_l - alpha tilde P_T W^{-1} G_l
     (computed as W^{-1/2}(T^ - alpha P_{T^} W^{-1/2} G_l), Lemma 3.5);
-    T_{l+1} = SVD^tt_r(W_l)."""
+    T_{l+1} = SVD^tt_r(W_l).
+    Variants: step="adaptive" takes the steepest step of Eq. (PRGD
+    stepsize) instead of Theorem 4.1's form; metric="uniform" sets every
+    G_{l,i} = I, which makes the iteration RGD (Section 3.1), whose constant
+    step is then alpha_scale / p (the limit of Theorem 4.1's form when
+    G_{l,i} -> eps I); retraction="weighted" is Remark 3.6's
+    W^{-1/2} SVD^tt_r W^{1/2}."""
     m = len(cores)
     N = idx.shape[0]
     p = N / float(np.prod(n))
     g = residual(cores, idx, y)
     if eps is None:
         eps = eps_from_residual(g, n, eps_rel)
-    if alpha is None:
-        alpha = alpha_from_eps(eps, p, alpha_scale)
-    G = metric_diagonals(g, idx, n, eps)
+    if metric == "uniform":
+        G = [np.ones(n[k]) for k in range(m)]
+    else:
+        G = metric_diagonals(g, idx, n, eps)
     # W^{-1} G_l = W^{-1/2} (W^{-1/2} G_l): project W^{-1/2} G_l at T^ ...
     That = scale_cores(cores, G, 1.0 / (4 * m))
     U, _ = left_orthogonalize(That)
     ahat = g * weight_entries(idx, G, -1.0 / (4 * m))
     A = tangent_project_hat(U, idx, ahat)
+    if alpha is None:
+        if step == "adaptive":
+            alpha = adaptive_step(U, A, G, idx)
+        elif metric == "uniform":
+            alpha = alpha_scale / p
+        else:
+            alpha = alpha_from_eps(eps, p, alpha_scale)
     C = assemble_2r(U, A, alpha, G)
-    new = tt_round(C, r)
+    if retraction == "weighted":
+        new = scale_cores(tt_round(scale_cores(C, G, 1.0 / (4 * m)), r), G, -1.0 / (4 * m))
+    else:
+        new = tt_round(C, r)
     info = StepInfo(eps, alpha, float(np.linalg.norm(g)))
     if keep:
         info.g = g
@@ -387,7 +443,7 @@ class SolveResult:
 
 
 def solve(cores, idx, y, n, r, truth=None, eps_rel=1.0, alpha_scale=1.0, max_iter=200,
-          tol=1e-10, stop_rule="relerr", eps_mode="adaptive"):
+          tol=1e-10, stop_rule="relerr", eps_mode="adaptive", **variants):
     """Iterate prgd_step.  stop_rule 'relerr': ||T-T*||/||T*|| <= tol (needs
     truth); 'step': ||T_{l+1}-T_l|| <= tol max(1, ||T_l||) (Section 5, noise
     experiment)."""
@@ -401,7 +457,7 @@ def solve(cores, idx, y, n, r, truth=None, eps_rel=1.0, alpha_scale=1.0, max_ite
             if eps_fixed is None:
                 eps_fixed = eps_from_residual(residual(cur, idx, y), n, eps_rel)
             kw["eps"] = eps_fixed
-        new, info = prgd_step(cur, idx, y, n, r, eps_rel=eps_rel, alpha_scale=alpha_scale, **kw)
+        new, info = prgd_step(cur, idx, y, n, r, eps_rel=eps_rel, alpha_scale=alpha_scale, **kw, **variants)
         if stop_rule == "relerr":
             err = tt_dist(new, truth) / tnorm
         else:

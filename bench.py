@@ -317,12 +317,17 @@ def ttc_arm(args):
     # iterations and time to rel.err <= 1e-6 (vs T*) for one problem, mixed and plain FP64
     P = probs[0]
     to_tol = {}
-    for name, prec in (("mixed", ttc.PREC_MIXED), ("fp64", ttc.PREC_FP64)):
-        with make_ctx(P, prec, ttc.STOP_RELERR, tol=1e-6, max_iter=200) as c2:
+    # (the steepest step and RGD -- uniform metric with the steepest step -- are
+    # the paper's comparison points, Section 5)
+    runs = (("mixed", ttc.PREC_MIXED, {}), ("fp64", ttc.PREC_FP64, {}),
+            ("steepest_mixed", ttc.PREC_MIXED, {"step_rule": ttc.STEP_STEEPEST}),
+            ("rgd_steepest_mixed", ttc.PREC_MIXED, {"step_rule": ttc.STEP_STEEPEST, "metric": ttc.METRIC_UNIFORM}))
+    for name, prec, var in runs:
+        with make_ctx(P, prec, ttc.STOP_RELERR, tol=1e-6, max_iter=200, **var) as c2:
             c2.set_truth(P.truth)
             res = c2.solve()
         iters = res["iters"]
-        with make_ctx(P, prec, ttc.STOP_NONE, max_iter=iters) as c3:
+        with make_ctx(P, prec, ttc.STOP_NONE, max_iter=iters, **var) as c3:
             c3.solve()                     # capture the graphs
             c3.set_cores(P.init)
             torch.cuda.synchronize()

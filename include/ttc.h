@@ -65,6 +65,26 @@ enum {
   TTC_STOP_RESID = 3   /* ||P_Omega(T_l) - y|| <= tol ||y|| (residual on Omega; no extra kernels) */
 };
 
+/* Step-size rules. */
+enum {
+  TTC_STEP_CONSTANT = 0, /* alpha_l = alpha_scale * sqrt(eps_l) / p (Theorem 4.1 form; alpha_scale / p with
+                            the uniform metric) */
+  TTC_STEP_STEEPEST = 1  /* alpha_l = ||Z||_W^2 / ||P_Omega Z||_F^2, Z = tilde P_T W^{-1} G_l: the exact line
+                            search along the search direction, Eq. (PRGD stepsize) in Section 3.2 */
+};
+
+/* Metrics. */
+enum {
+  TTC_METRIC_PRECOND = 0, /* W_l from G_{l,i} = eps I + diag(M_i(G_l) M_i(G_l)^T) (Section 3.2) */
+  TTC_METRIC_UNIFORM = 1  /* G_{l,i} = I: the iteration is RGD (Section 3.1) */
+};
+
+/* Retractions. */
+enum {
+  TTC_RETRACT_PLAIN = 0,   /* T_{l+1} = SVD^tt_r(W_l) (Algorithm 2) */
+  TTC_RETRACT_WEIGHTED = 1 /* T_{l+1} = W^{-1/2} SVD^tt_r(W^{1/2} W_l) (Remark 3.6) */
+};
+
 typedef struct {
   int precision;        /* TTC_PREC_* */
   double eps_rel;       /* eps_l = eps_rel * ||G_l||_F^2 / min_k n_k (reading of Section 3.2) */
@@ -76,6 +96,9 @@ typedef struct {
   int check_every;      /* evaluate the stop rule every k iterations (>= 1) */
   double polish_below;  /* MIXED: switch to FP64 once the relative residual is below this */
   int use_graph;        /* nonzero: replay one CUDA graph per iteration */
+  int step_rule;        /* TTC_STEP_* */
+  int metric;           /* TTC_METRIC_* */
+  int retraction;       /* TTC_RETRACT_* */
 } ttc_options;
 
 typedef struct {
@@ -96,7 +119,7 @@ typedef struct {
 
 /* Fill `opt` with defaults: MIXED precision, eps_rel 1, alpha_scale 1.5,
  * tol 1e-6, max_iter 500, stop rule RELERR, check_every 1, polish_below 1e-5,
- * graphs on. */
+ * graphs on, constant step, preconditioned metric, plain retraction. */
 void ttc_default_options(ttc_options* opt);
 
 /* Create a context for order d (1 < d <= 16), mode sizes n[d] (n_k >= 1),

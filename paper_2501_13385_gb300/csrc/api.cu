@@ -156,6 +156,9 @@ void ttc_default_options(ttc_options* o) {
   o->check_every = 1;
   o->polish_below = 1e-5;
   o->use_graph = 1;
+  o->step_rule = TTC_STEP_CONSTANT;
+  o->metric = TTC_METRIC_PRECOND;
+  o->retraction = TTC_RETRACT_PLAIN;
 }
 
 const char* ttc_strerror(int s) {
@@ -221,6 +224,14 @@ int ttc_create(ttc_ctx** out, int d, const int64_t* n, const int32_t* r, const t
   P.R = c->rank_bucket;
   P.dstar = ovf ? 0 : dl;
   P.inv_min_n = 1.0 / (double)minn;
+  if (c->opt.step_rule < 0 || c->opt.step_rule > 1 || c->opt.metric < 0 || c->opt.metric > 1 ||
+      c->opt.retraction < 0 || c->opt.retraction > 1 || c->opt.precision < 0 || c->opt.precision > 2) {
+    delete c;
+    return TTC_EINVAL;
+  }
+  P.steepest = c->opt.step_rule == TTC_STEP_STEEPEST;
+  P.uniform = c->opt.metric == TTC_METRIC_UNIFORM;
+  P.weighted_retraction = c->opt.retraction == TTC_RETRACT_WEIGHTED;
   (void)dstar;
   int s = TTC_OK;
   if (cuda_stream) {

@@ -32,6 +32,9 @@ struct DevProb {
   double p;                    // N / d*
   double inv_min_n;            // 1 / min_k n_k
   int keep_residual;           // write g[] in input order during the pass
+  int steepest;                // step size by exact line search (Eq. (PRGD stepsize))
+  int uniform;                 // G_{l,i} = I (RGD)
+  int weighted_retraction;     // Remark 3.6: W^{-1/2} SVD^tt_r W^{1/2}
 
   // current iterate
   double* core64[TTC_MAXM];    // FP64 master, slice-major, unpadded
@@ -79,6 +82,9 @@ struct DevProb {
   // outputs of the Omega pass
   double* s[TTC_MAXM];           // slice energies, n_k
   double* E[TTC_MAXM];           // n_k x r_k x r_{k+1}
+  double* B1[TTC_MAXM];          // steepest step: update cores at unit step, n_k x r_k x r_{k+1}
+  double* zw;                    // steepest step: per slice G^{1/(2m)} <Lam B1 Gam, B1> (all modes)
+  double* tpart;                 // steepest step: block partials of ||P_Omega Z||^2
   double* g;                     // residual in input order (when keep_residual)
 
   // dense-stage buffers

@@ -100,8 +100,10 @@ __device__ __forceinline__ double inv_root(double v, int m) {
   for (int it = 0; it < 2; ++it) y = y * fma(c, fma(-v, ipow_2m(y, two_m), 1.0), 1.0);
   return y;
 }
-// G_k(x)^{+1/(2m)} (sign > 0) or G_k(x)^{-1/(2m)} (sign < 0)
+// G_k(x)^{+1/(2m)} (sign > 0) or G_k(x)^{-1/(2m)} (sign < 0); 1 with the
+// uniform metric (RGD)
 __device__ __forceinline__ double gpow(const DevProb& P, int k, int x, int sign) {
+  if (P.uniform) return 1.0;
   const double v = P.scal[SC_EPS] + P.s[k][x];
   const double y = inv_root(v, P.m);            // v^{-1/(2m)}
   return sign < 0 ? y : v * ipow_2m(y, 2 * P.m - 1);   // v^{1/(2m)} = v * y^{2m-1}
@@ -408,12 +410,15 @@ __device__ void slice_map(const DevProb& P, int k, int x, double* Y) {
     __syncthreads();
     Cp = Y;
   }
+  // Remark 3.6: the rounding ran on W^{1/2} W_l; undo the weight
+  const double wu = P.weighted_retraction ? sqrt(gpow(P, k, x, -1)) : 1.0;
   if (k < m - 1) {
     const double* Pk = P.small + P.off_pk[k];
     for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
       int a = i / rb, b = i - (i / rb) * rb;
       double acc = 0.0;
       for (int t = 0; t < qb; ++t) acc = fma(Cp[a * qb + t], Pk[t * rb + b], acc);
+      acc *= wu;
       T[i] = acc;
       T32[pad_idx(P, k, a, b)] = (float)acc;
       T64[pad_idx(P, k, a, b)] = acc;
@@ -421,9 +426,10 @@ __device__ void slice_map(const DevProb& P, int k, int x, double* Y) {
   } else {
     for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
       int a = i / rb, b = i - (i / rb) * rb;
-      T[i] = Cp[i];
-      T32[pad_idx(P, k, a, b)] = (float)Cp[i];
-      T64[pad_idx(P, k, a, b)] = Cp[i];
+      const double v = Cp[i] * wu;
+      T[i] = v;
+      T32[pad_idx(P, k, a, b)] = (float)v;
+      T64[pad_idx(P, k, a, b)] = v;
     }
   }
 }
@@ -650,9 +656,10 @@ __device__ void warp_slice_map(const DevProb& P, int k, int x, double* scr) {
   double* T = P.core64[k] + (long long)x * ra * rb;
   float* T32 = P.core32p[k] + (long long)x * P.R * P.R;
   double* T64 = P.core64p[k] + (long long)x * P.R * P.R;
+  const double wu = P.weighted_retraction ? sqrt(gpow(P, k, x, -1)) : 1.0;   // Remark 3.6
   for (int i = lane; i < ra * rb; i += 32) {
     const int a = i / rb, b = i - (i / rb) * rb;
-    const double v = Tn[i];
+    const double v = Tn[i] * wu;
     T[i] = v;
     T32[pad_idx(P, k, a, b)] = (float)v;
     T64[pad_idx(P, k, a, b)] = v;
@@ -765,6 +772,7 @@ __global__ void __launch_bounds__(kThreads) k_build_C_w(const DevProb P, int nsl
   }
   const int qa = P.q[k], qb = P.q[k + 1];
   double* C = P.C[k] + (long long)x * qa * qb;
+  const double ws = P.weighted_retraction ? sqrt(gpow(P, k, x, +1)) : 1.0;   // Remark 3.6: W^{1/2} W_l
   for (int i = lane; i < qa * qb; i += 32) {
     int a = i / qb, b = i - (i / qb) * qb;
     double v;
@@ -778,9 +786,127 @@ __global__ void __launch_bounds__(kThreads) k_build_C_w(const DevProb P, int nsl
       else
         v = (b < rb) ? B[(a - ra) * rb + b] : Tt[(a - ra) * rb + (b - rb)];
     }
-    C[i] = v;
+    C[i] = v * ws;
   }
 }
+
+// ---- steepest step, Eq. (PRGD stepsize) ------------------------------------
+// One block per slice (k, x): the update core at unit step
+//   B1_k(x) = -[G_k(x)^{-1/(2m)} Lam_k^{-1} E_k(x) Gam_{k+1}^{-1} - T_k(x) Q_k]
+// (W_l = T_l + sum_k [T..alpha B1_k..T], so Z = tilde P_T W^{-1} G_l =
+// -sum_k [T..B1_k..T]) and G_k(x)^{1/(2m)} <Lam_k B1_k(x) Gam_{k+1}, B1_k(x)>:
+// summed over all slices this is ||Z||_W^2, because the components of Z are
+// W-orthogonal (Lemma 3.4) and Lam, Gam are the Grams of W^{1/2} T.
+__global__ void __launch_bounds__(128) k_build_B1(const DevProb P) {
+  __shared__ double t1[TTC_MAXR * TTC_MAXR];
+  __shared__ double B[TTC_MAXR * TTC_MAXR];
+  __shared__ double red[128];
+  const int slice = blockIdx.x;
+  int blk = slice, k = 0;
+  while (k < P.m - 1 && blk >= P.n[k]) {
+    blk -= P.n[k];
+    ++k;
+  }
+  const int x = blk, m = P.m;
+  const int ra = P.r[k], rb = P.r[k + 1];
+  const double wi = gpow(P, k, x, -1);
+  const double* T = P.core64[k] + (long long)x * ra * rb;
+  const double* E = P.E[k] + (long long)x * ra * rb;
+  blk_gemm<double>(ra, rb, ra, P.small + P.off_lami[k], ra, false, E, rb, false, t1, rb, 1.0, false);
+  __syncthreads();
+  blk_gemm<double>(ra, rb, rb, t1, rb, false, P.small + P.off_gami[k + 1], rb, false, B, rb, -wi, false);
+  __syncthreads();
+  if (k + 1 < m) {
+    blk_gemm<double>(ra, rb, rb, T, rb, false, P.small + P.off_qm[k], rb, false, B, rb, 1.0, true);
+    __syncthreads();
+  }
+  double* out = P.B1[k] + (long long)x * ra * rb;
+  for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) out[i] = B[i];
+  blk_gemm<double>(ra, rb, ra, P.small + P.off_lam[k], ra, false, B, rb, false, t1, rb, 1.0, false);   // Lam B1
+  __syncthreads();
+  const double* Gm = P.small + P.off_gam[k + 1];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
+    const int a = i / rb, b = i - (i / rb) * rb;
+    double v = 0.0;
+    for (int t = 0; t < rb; ++t) v = fma(t1[a * rb + t], Gm[t * rb + b], v);
+    acc = fma(v, B[i], acc);
+  }
+  const double tot = blk_sum(acc, red);
+  if (threadIdx.x == 0) P.zw[slice] = gpow(P, k, x, +1) * tot;
+}
+
+// ||P_Omega Z||^2 = sum over Omega of (sum_k l_{k-1} B1_k(x_k) r_{k+1})^2: the
+// tangent TT [[T, 0], [B1, T]] evaluated entry by entry along the chain
+// (l_T, l_Z) <- (l_T T_k(x_k), l_Z T_k(x_k) + l_T B1_k(x_k)) in FP64, in the
+// mode-1 order of Omega; block partials, then the last block forms
+// alpha_l = ||Z||_W^2 / ||P_Omega Z||^2 (an explicit step size, when given,
+// is kept).
+constexpr int kTanThreads = 256;
+constexpr int kTanCounter = 127;
+
+template <int R>
+__global__ void __launch_bounds__(kTanThreads) k_tangent_sq(const DevProb P, int nslices) {
+  __shared__ double red[kTanThreads];
+  __shared__ int am_last;
+  double acc = 0.0;
+  for (int e = blockIdx.x * kTanThreads + threadIdx.x; e < P.N; e += gridDim.x * kTanThreads) {
+    const Code w = load_code(P, 0, e);
+    double lT[R], lZ[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      lT[a] = 0.0;
+      lZ[a] = 0.0;
+    }
+    lT[0] = 1.0;
+    for (int k = 0; k < P.m; ++k) {
+      const int x = code_coord(P, w, k);
+      const int ra = P.r[k], rb = P.r[k + 1];
+      const double* S = P.core64[k] + (long long)x * ra * rb;
+      const double* Bk = P.B1[k] + (long long)x * ra * rb;
+      double nT[R], nZ[R];
+#pragma unroll
+      for (int b = 0; b < R; ++b) {
+        nT[b] = 0.0;
+        nZ[b] = 0.0;
+        if (b < rb) {
+#pragma unroll
+          for (int a = 0; a < R; ++a) {
+            if (a >= ra) break;
+            const double sv = __ldg(S + a * rb + b);
+            nT[b] = fma(lT[a], sv, nT[b]);
+            nZ[b] = fma(lZ[a], sv, fma(lT[a], __ldg(Bk + a * rb + b), nZ[b]));
+          }
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < R; ++b) {
+        lT[b] = nT[b];
+        lZ[b] = nZ[b];
+      }
+    }
+    acc = fma(lZ[0], lZ[0], acc);
+  }
+  const double tot = blk_sum(acc, red);
+  if (threadIdx.x == 0) P.tpart[blockIdx.x] = tot;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(P.counters + kTanCounter, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  double den = 0.0, num = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += kTanThreads) den += __ldcg(P.tpart + i);
+  den = blk_sum(den, red);
+  for (int i = threadIdx.x; i < nslices; i += kTanThreads) num += __ldcg(P.zw + i);
+  num = blk_sum(num, red);
+  if (threadIdx.x == 0) {
+    if (!(P.scal[SC_ALPHA_OVR] > 0.0)) P.scal[SC_ALPHA] = den > 0.0 ? num / den : 0.0;
+    P.counters[kTanCounter] = 0;
+  }
+}
+
+inline int tangent_blocks(const DevProb& P) { return std::max(1, std::min((P.N + kTanThreads - 1) / kTanThreads, 2 * 152)); }
 
 // one block per slice (k, x): B_k(x) and the block core C_k(x)
 __global__ void __launch_bounds__(128) k_build_C(const DevProb P) {
@@ -807,6 +933,7 @@ __global__ void __launch_bounds__(128) k_build_C(const DevProb P) {
   }
   const int qa = P.q[k], qb = P.q[k + 1];
   double* C = P.C[k] + (long long)x * qa * qb;
+  const double ws = P.weighted_retraction ? sqrt(gpow(P, k, x, +1)) : 1.0;   // Remark 3.6: W^{1/2} W_l
   for (int i = threadIdx.x; i < qa * qb; i += blockDim.x) {
     int a = i / qb, b = i - (i / qb) * qb;
     double v;
@@ -820,7 +947,7 @@ __global__ void __launch_bounds__(128) k_build_C(const DevProb P) {
       else
         v = (b < rb) ? B[(a - ra) * rb + b] : T[(a - ra) * rb + (b - rb)];
     }
-    C[i] = v;
+    C[i] = v * ws;
   }
 }
 
@@ -1021,6 +1148,17 @@ int ttc_alloc_dense(ttc_ctx* c) {
     TTC_TRY(ttc_alloc(c, (void**)&pv, sizeof(double) * (size_t)c->n[k] * c->r[k] * c->r[k + 1], false));
     P.prev64[k] = pv;
   }
+  if (P.steepest) {
+    long long nsl = 0;
+    for (int k = 0; k < m; ++k) {
+      double* b1 = nullptr;
+      TTC_TRY(ttc_alloc(c, (void**)&b1, sizeof(double) * (size_t)c->n[k] * c->r[k] * c->r[k + 1], false));
+      P.B1[k] = b1;
+      nsl += c->n[k];
+    }
+    TTC_TRY(ttc_alloc(c, (void**)&P.zw, sizeof(double) * (size_t)nsl, false));
+    TTC_TRY(ttc_alloc(c, (void**)&P.tpart, sizeof(double) * 2 * 152, false));
+  }
   double* scal = nullptr;
   TTC_TRY(ttc_alloc(c, (void**)&scal, sizeof(double) * SC_COUNT, false));
   TTC_CUDA(cudaMemset(scal, 0, sizeof(double) * SC_COUNT));
@@ -1103,7 +1241,7 @@ int ttc_alloc_dense(ttc_ctx* c) {
       pl.metric[which].push_back(S);   // AB and BB jobs are added at launch (B's ranks)
     }
   }
-  if (ctr > 128) return TTC_EUNSUPPORTED;
+  if (ctr > kTanCounter) return TTC_EUNSUPPORTED;
   long long metric_extra = 0;
   for (int k = 0; k < m; ++k) metric_extra += 2LL * nblocks_for((int)c->n[k]) * TTC_MAXR * TTC_MAXR;
   double* redp = nullptr;
@@ -1155,6 +1293,19 @@ int ttc_launch_dense(ttc_ctx* c) {
   for (auto& S : pl.gram) TTC_TRY(run_stage(c, pl, S));
   int nslices = 0;
   for (int k = 0; k < m; ++k) nslices += (int)c->n[k];
+  if (P.steepest) {   // alpha_l by exact line search before the rank-2r cores are formed
+    k_build_B1<<<nslices, 128, 0, st>>>(P);
+    TTC_CUDA(cudaGetLastError());
+    const int tb = tangent_blocks(P);
+    switch (c->rank_bucket) {
+      case 4: k_tangent_sq<4><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+      case 8: k_tangent_sq<8><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+      case 16: k_tangent_sq<16><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+      default: k_tangent_sq<32><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+    }
+    TTC_CUDA(cudaGetLastError());
+    c->nlaunch += 2;
+  }
   if (pl.warp)
     k_build_C_w<<<(nslices + kWarpsW - 1) / kWarpsW, kThreads, sizeof(double) * kWarpsW * kWScr, st>>>(P, nslices);
   else

@@ -140,7 +140,11 @@ __device__ __forceinline__ void segment_reduce_block(const DevProb& P, int blk, 
     const double g2 = sh[0];
     const double eps = P.scal[SC_EPS_FIXED] > 0.0 ? P.scal[SC_EPS_FIXED]
                                                   : fmax(P.scal[SC_EPS_REL] * g2 * P.inv_min_n, 1e-300);
-    const double alpha = P.scal[SC_ALPHA_OVR] > 0.0 ? P.scal[SC_ALPHA_OVR] : P.scal[SC_ALPHA_SCALE] * sqrt(eps) / P.p;
+    // Theorem 4.1's form; with the uniform metric (RGD) its limit alpha_scale / p.
+    // The steepest-step rule overwrites alpha after the dense stage's projection.
+    const double alpha = P.scal[SC_ALPHA_OVR] > 0.0 ? P.scal[SC_ALPHA_OVR]
+                         : P.uniform            ? P.scal[SC_ALPHA_SCALE] / P.p
+                                                : P.scal[SC_ALPHA_SCALE] * sqrt(eps) / P.p;
     P.scal[SC_G2] = g2;
     P.scal[SC_EPS] = eps;
     P.scal[SC_ALPHA] = alpha;

@@ -17,6 +17,9 @@ LIB_PATH = os.path.join(HERE, "libttc.so")
 
 PREC_FP64, PREC_MIXED, PREC_FP32 = 0, 1, 2
 STOP_RELERR, STOP_STEP, STOP_NONE, STOP_RESID = 0, 1, 2, 3
+STEP_CONSTANT, STEP_STEEPEST = 0, 1
+METRIC_PRECOND, METRIC_UNIFORM = 0, 1
+RETRACT_PLAIN, RETRACT_WEIGHTED = 0, 1
 
 STATUS = {
     0: "TTC_OK", -1: "TTC_EINVAL", -2: "TTC_ENOMEM", -3: "TTC_ERANGE", -4: "TTC_EDUP",
@@ -39,6 +42,7 @@ class Options(C.Structure):
         ("precision", C.c_int), ("eps_rel", C.c_double), ("alpha_scale", C.c_double),
         ("eps_frozen", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("stop_rule", C.c_int),
         ("check_every", C.c_int), ("polish_below", C.c_double), ("use_graph", C.c_int),
+        ("step_rule", C.c_int), ("metric", C.c_int), ("retraction", C.c_int),
     ]
 
 

@@ -338,6 +338,23 @@ def ttc_arm(args):
         to_tol[name] = {"iters": iters, "converged": res["converged"], "ms": 1e3 * dt,
                         "polish_iter": res["polish_iter"]}
 
+    # the tomography-shaped workload of Section 5 (order 10, mode 4, ranks 4,
+    # 80 000 entries): iterations and time to rel.err <= 1e-6, mixed precision
+    Q = w.qst_like(rank)
+    with make_ctx(Q, ttc.PREC_MIXED, ttc.STOP_RELERR, tol=1e-6, max_iter=200) as c2:
+        c2.set_truth(Q.truth)
+        qres = c2.solve()
+    with make_ctx(Q, ttc.PREC_MIXED, ttc.STOP_NONE, max_iter=qres["iters"]) as c3:
+        c3.solve()
+        c3.set_cores(Q.init)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c3.solve()
+        torch.cuda.synchronize()
+        qdt = time.perf_counter() - t0
+    qst = {"workload": "qst_like", "qubits": 10, "ranks": 4, "omega": Q.N, "iters": qres["iters"],
+           "converged": qres["converged"], "ms": 1e3 * qdt}
+
     # end to end through the public API from pinned host buffers: every step
     # copies all B problems' observations and starting cores in, runs
     # e2e_iters batched iterations and reads all cores back
@@ -434,6 +451,7 @@ def ttc_arm(args):
             "problem_iters_per_s": B * 1e3 / ms_per_step,
             "step_ms_p50": statistics.median(step_ms), "step_ms_p99": sorted(step_ms)[max(0, int(0.99 * K) - 1)],
             "to_rel_err_1e-6": to_tol,
+            "qst_to_rel_err_1e-6": qst,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "Ω-entries/s", "h2d_bytes_per_step": h2d,

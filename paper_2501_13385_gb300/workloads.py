@@ -339,6 +339,93 @@ def tomography_like(seed: int = 0, order: int = 12, mode: int = 4, interior: int
     return _finish("tomography_like", n, r, cores, rng, count, noise_std, "abs", 0.05, seed)
 
 
+# Pauli matrices sigma_1..sigma_4 = I, X, Y, Z (Section 5, quantum state tomography)
+PAULI = np.array([[[1, 0], [0, 1]], [[0, 1], [1, 0]], [[0, -1j], [1j, 0]], [[1, 0], [0, -1]]], dtype=np.complex128)
+
+
+def hermitian_basis(s: int) -> np.ndarray:
+    """An orthonormal basis (Frobenius inner product) of the s x s Hermitian
+    matrices over the reals: E_ii, (E_ij + E_ji)/sqrt2, i(E_ij - E_ji)/sqrt2."""
+    out = []
+    for i in range(s):
+        e = np.zeros((s, s), dtype=np.complex128)
+        e[i, i] = 1.0
+        out.append(e)
+    for i in range(s):
+        for j in range(i + 1, s):
+            e = np.zeros((s, s), dtype=np.complex128)
+            e[i, j] = e[j, i] = 1.0 / math.sqrt(2.0)
+            out.append(e)
+            f = np.zeros((s, s), dtype=np.complex128)
+            f[i, j] = -1j / math.sqrt(2.0)
+            f[j, i] = 1j / math.sqrt(2.0)
+            out.append(f)
+    return np.stack(out)
+
+
+def random_mps(rng: Rng, qubits: int, bond: int) -> List[np.ndarray]:
+    """Random matrix product state u = [U_1..U_n], U_k in C^{s_{k-1} x 2 x s_k}
+    (s_0 = s_n = 1, interior s = bond), complex Gaussian entries, scaled to
+    ||u|| = 1 (so rho = u u^dagger has unit trace)."""
+    s = [1] + [bond] * (qubits - 1) + [1]
+    cores = []
+    for k in range(qubits):
+        sz = s[k] * 2 * s[k + 1]
+        re, im = rng.normal(sz), rng.normal(sz)
+        cores.append((re + 1j * im).reshape(s[k], 2, s[k + 1]))
+    # ||u||^2 by the transfer-matrix recursion
+    env = np.ones((1, 1), dtype=np.complex128)
+    for U in cores:
+        env = np.einsum("ab,aic,bid->cd", env, U, U.conj())
+    nrm = math.sqrt(float(env.real[0, 0]))
+    return [U / nrm ** (1.0 / qubits) for U in cores]
+
+
+def pauli_measurement_cores(mps: Sequence[np.ndarray]) -> List[np.ndarray]:
+    """Real TT cores of T*(a) = Tr(rho W_a), rho = u u^dagger, W_a = sigma_{a_1}
+    (x) ... (x) sigma_{a_n} (Section 5).  The left partial products of the
+    MPO rho (bond pairs (beta, beta') of the MPS) are Hermitian s x s matrices,
+    transported by M -> sum_{i,j} sigma(j, i) U_i^T M conj(U_j); expanding
+    them in a real orthonormal basis of the Hermitian matrices gives real
+    cores of TT-rank s_k^2."""
+    n = len(mps)
+    out = []
+    bases = [hermitian_basis(U.shape[0]) for U in mps] + [hermitian_basis(1)]
+    for k, U in enumerate(mps):
+        Hin, Hout = bases[k], bases[k + 1]
+        core = np.zeros((len(Hin), 4, len(Hout)))
+        for alpha in range(4):
+            sig = PAULI[alpha]
+            for c, Hc in enumerate(Hin):
+                # T_alpha(H_c) = sum_{i,j} sigma(j, i) U_i^T H_c conj(U_j)
+                M = np.zeros((U.shape[2], U.shape[2]), dtype=np.complex128)
+                for i in range(2):
+                    for j in range(2):
+                        if sig[j, i] != 0:
+                            M += sig[j, i] * (U[:, i, :].T @ Hc @ U[:, j, :].conj())
+                for c2, Hd in enumerate(Hout):
+                    core[c, alpha, c2] = float(np.real(np.trace(Hd.conj().T @ M)))
+        out.append(core)
+    return out
+
+
+def qst_like(seed: int = 0, qubits: int = 10, bond: int = 2, oversampling: float = 200.0,
+             init_rel: float = 0.05) -> Problem:
+    """Quantum state tomography workload (Section 5): a random MPS with bond
+    dimension `bond`, rho = u u^dagger (an MPO of bond dimension bond^2), and
+    its Pauli-measurement tensor T*(a) = Tr(rho W_a), an order-`qubits` real
+    tensor with mode size 4 and TT-ranks (1, bond^2, ..., bond^2, 1).
+    |Omega| = oversampling x (manifold dimension): 80 000 entries (7.6%) for
+    10 qubits and bond 2, as in the paper's experiment.  Noiseless."""
+    rng = Rng(seed, 8)
+    mps = random_mps(rng, qubits, bond)
+    truth = pauli_measurement_cores(mps)
+    n = [4] * qubits
+    r = [1] + [c.shape[2] for c in truth[:-1]] + [1]
+    count = min(int(round(oversampling * oversampling_dim(n, r))), math.prod(n))
+    return _finish("qst_like", n, r, truth, rng, count, 0.0, "abs", init_rel, seed)
+
+
 def random_request(seed: int, max_entries: int = 1_000_000) -> Problem:
     """One request of the mixed serving stream: order in [3, 12], mode size in
     [4, 256], interior rank in [2, 16], |Omega| log-uniform in [1e3, 1e6].

@@ -118,3 +118,22 @@ def test_steepest_mixed_solve_recovers_orthogonal_cubic():
         res = c.solve()
         assert res["converged"]
         assert c.relerr() <= 1e-6
+
+
+def test_qst_workload_fp64_steps_match_oracle():
+    # order 10, mode 4, TT-ranks 4 (the tomography experiment's shape, Section 5)
+    P = w.qst_like(1, init_rel=0.1)
+    cur = P.init
+    with ctx_for(P, precision=ttc.PREC_FP64) as c:
+        for _ in range(2):
+            c.step()
+            cur, _ = o.prgd_step(cur, P.idx, P.y, P.n, P.r, eps_rel=1.0, alpha_scale=1.5)
+            assert o.tt_dist(c.get_cores(), cur) <= 1e-9 * o.tt_norm(cur)
+
+
+def test_qst_workload_mixed_solve_converges():
+    P = w.qst_like(2)
+    with ctx_for(P, precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_RELERR, tol=1e-6, max_iter=400) as c:
+        c.set_truth(P.truth)
+        res = c.solve()
+        assert res["converged"], res

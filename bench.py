@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--e2e-iters", type=int, default=20)
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="requests streamed through the serving engine (0: skip)")
+    ap.add_argument("--serve-mixed", type=int, default=32,
+                    help="requests of the mixed serving stream (0: skip)")
     ap.add_argument("--batch", type=int, default=32,
                     help="independent problems per step (one CUDA graph launch); 1 = a single problem")
     return ap.parse_args()
@@ -456,6 +458,46 @@ def ttc_arm(args):
             "gpu_launches": s1["launches"] - s0["launches"],
         }
 
+    # the mixed serving stream (orders 3-12, modes 4-256, ranks 2-16, |Omega|
+    # log-uniform, capped at 2e5 here to keep the run short): a burst of all
+    # requests, then Poisson arrivals at 70% of the burst's request rate
+    mixed = None
+    if args.serve_mixed > 0:
+        reqs = [w.random_request(1000 + i, max_entries=200_000) for i in range(args.serve_mixed)]
+        # a stream of unknown problems takes the steepest step: the constant
+        # step's tuned scale diverges on some high-order, low-oversampling draws
+        mopt = ttc.default_options(precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_RELERR, tol=1e-6, max_iter=500,
+                                   step_rule=ttc.STEP_STEEPEST)
+
+        def run_stream(gaps):
+            with ttc.Server(max_slots=B) as srv:
+                t0 = time.perf_counter()
+                tk = []
+                for Q, gap in zip(reqs, gaps):
+                    if gap > 0:
+                        time.sleep(gap)
+                    tk.append(srv.submit(Q.n, Q.r, Q.idx, Q.y, Q.init, truth=Q.truth, options=mopt))
+                rs = [srv.poll(t, cores=False) for t in tk]
+                wall_s = time.perf_counter() - t0
+                st = srv.stats()
+            lat = sorted(r["latency_ms"] for r in rs)
+            q = lambda f: lat[min(len(lat) - 1, max(0, int(np.ceil(f * len(lat))) - 1))]
+            return {"requests": len(rs), "wall_ms": 1e3 * wall_s, "requests_per_s": len(rs) / wall_s,
+                    "latency_p50_ms": q(0.5), "latency_p99_ms": q(0.99),
+                    "converged": sum(1 for r in rs if r["converged"]),
+                    "failed": sum(1 for r in rs if r["status"] not in ("TTC_OK", "TTC_ENOTCONV")),
+                    "mean_iters": float(np.mean([r["iters"] for r in rs])),
+                    "entry_iters_per_s": st["entry_iterations"] / wall_s}
+        burst = run_stream([0.0] * len(reqs))
+        prng = np.random.default_rng(7)
+        rate = 0.7 * burst["requests_per_s"]
+        poisson = run_stream(list(prng.exponential(1.0 / rate, len(reqs))))
+        poisson["arrival_rate_per_s"] = rate
+        mixed = {"workload": "random_request stream (orders 3-12, modes 4-256, ranks 2-16, |Omega| <= 2e5)",
+                 "stop": "rel.err <= 1e-6 vs T* or 500 iterations, mixed precision, steepest step",
+                 "max_slots": B,
+                 "burst": burst, "poisson_70pct": poisson}
+
     # roofline of the dominant kernel: the batched sampled pass, one launch per step
     peaks = {}
     try:
@@ -507,6 +549,7 @@ def ttc_arm(args):
                     "ms_per_step": e2e_step_ms},
             "gpu_launches": launches,
             "serving": serving,
+            "serving_mixed_stream": mixed,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

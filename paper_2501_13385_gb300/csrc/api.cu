@@ -450,11 +450,23 @@ void ttc_solve_after(ttc_ctx* c, SolveState& st, const double* sc, bool checked)
   }
   st.info.res_norm = std::sqrt(sc[SC_G2]);
   const double rel_res = std::sqrt(sc[SC_G2] / std::fmax(c->ynorm2, 1e-300));
+  if (!std::isfinite(rel_res)) {
+    st.status = TTC_ENONFINITE;
+    st.done = true;
+    return;
+  }
   if (c->opt.precision == TTC_PREC_MIXED && c->cur_prec != TTC_PREC_FP64 && rel_res <= c->opt.polish_below) {
     c->cur_prec = TTC_PREC_FP64;
     st.info.polish_iter = st.it + 1;
   }
   const bool polishing_done = (c->opt.precision != TTC_PREC_MIXED) || c->cur_prec == TTC_PREC_FP64;
+  if (checked && (c->opt.stop_rule == TTC_STOP_RELERR || c->opt.stop_rule == TTC_STOP_STEP) &&
+      !(std::isfinite(sc[SC_METRIC]) && std::isfinite(sc[SC_NORM]))) {
+    // the new iterate is not finite: never read that as convergence
+    st.status = TTC_ENONFINITE;
+    st.done = true;
+    return;
+  }
   double metric = -1.0;
   if (c->opt.stop_rule == TTC_STOP_RESID) {
     metric = rel_res;

@@ -238,6 +238,7 @@ __device__ void post_small_proj(const DevProb& P, double* sm) {
 __device__ void orthonormalize(const double* W, int q, int r, double* U, double* s, double* red, float* Lf,
                                float* Lif, int* bad) {
   const int tid = threadIdx.x;
+  __shared__ int pow2[1];
   double* Z = s;
   double* Z2 = Z + q * r;
   double* G = Z2 + q * r;
@@ -249,14 +250,14 @@ __device__ void orthonormalize(const double* W, int q, int r, double* U, double*
   for (int pass = 0; pass < 2; ++pass) {
     blk_gemm<double>(r, r, q, src, r, true, src, r, false, G, r, 1.0, false);   // G = src^T src
     __syncthreads();
-    if (tid < 32) warp_chol_inv32(G, r, r, Lf, Lif);
+    if (tid < 32) warp_chol_inv32(G, r, r, Lf, Lif, &pow2[0]);
     __syncthreads();
     double* dst = (pass == 0) ? Z : Z2;
     for (int i = tid; i < q * r; i += blockDim.x) {                               // dst = src L^{-T}
       int a = i / r, c = i - (i / r) * r;
       double acc = 0.0;
       for (int t = 0; t <= c; ++t) acc = fma(src[a * r + t], (double)Lif[c * r + t], acc);
-      dst[i] = acc;
+      dst[i] = ldexp(acc, -pow2[0]);
     }
     __syncthreads();
     blk_gemm<double>(r, r, q, dst, r, true, dst, r, false, E, r, 1.0, false);   // E = dst^T dst - I
@@ -265,7 +266,7 @@ __device__ void orthonormalize(const double* W, int q, int r, double* U, double*
     for (int i = tid; i < r * r; i += blockDim.x) {
       double v = E[i] - (((i / r) == (i % r)) ? 1.0 : 0.0);
       E[i] = v;
-      em = fmax(em, fabs(v));
+      em = nanmax(em, fabs(v));
     }
     em = blk_max(em, red);
     if (em < 1e-4) {   // polish: F = I - E/2 + 3/8 E^2, U = dst F
@@ -310,7 +311,30 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
   for (int i = tid; i < q * q; i += blockDim.x) N[i] = P.small[P.off_nk[k] + i];
   if (tid == 0) bad = 0;
   __syncthreads();
-  blk_gemm<double>(q, q, q, P.small + P.off_psi[k + 1], q, false, N, q, false, A, q, 1.0, false);
+  {
+    // A = Psi N from operands scaled by powers of two to unit size: its
+    // invariant subspaces do not depend on the scale, and Psi N itself grows
+    // with the fourth power of the iterate's entries
+    const double* Psi = P.small + P.off_psi[k + 1];
+    double mp = 0.0, mn = 0.0;
+    for (int i = tid; i < q * q; i += blockDim.x) {
+      mp = nanmax(mp, fabs(Psi[i]));
+      mn = nanmax(mn, fabs(N[i]));
+    }
+    mp = blk_max(mp, red);
+    mn = blk_max(mn, red);
+    int ep = 0, en = 0;
+    if (mp > 0.0 && mp <= 1.7e308) frexp(mp, &ep);
+    if (mn > 0.0 && mn <= 1.7e308) frexp(mn, &en);
+    double* Ps = scr;   // q*q <= 2 q r
+    double* Ns = W;     // W and V: 2 q r >= q*q doubles
+    for (int i = tid; i < q * q; i += blockDim.x) {
+      Ps[i] = ldexp(Psi[i], -ep);
+      Ns[i] = ldexp(N[i], -en);
+    }
+    __syncthreads();
+    blk_gemm<double>(q, q, q, Ps, q, false, Ns, q, false, A, q, 1.0, false);
+  }
   // start: the coordinates of the iterate's own part (last r of the 2r bond)
   for (int i = tid; i < q * r; i += blockDim.x) {
     int a = i / r, c = i - (i / r) * r;
@@ -351,12 +375,13 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
   __syncthreads();
   blk_gemm<double>(r, r, q, U, r, true, W, r, false, G, r, 1.0, false);          // G = U^T N U
   __syncthreads();
-  if (tid < 32) warp_chol_inv32(G, r, r, Lf, Lif);
+  __shared__ int pow2n[1];
+  if (tid < 32) warp_chol_inv32(G, r, r, Lf, Lif, &pow2n[0]);
   __syncthreads();
   double* Rinv = Bm;
   for (int i = tid; i < r * r; i += blockDim.x) {                                 // Rinv = L^{-T}
     int a = i / r, c = i - (i / r) * r;
-    Rinv[i] = (double)Lif[c * r + a];
+    Rinv[i] = ldexp((double)Lif[c * r + a], -pow2n[0]);
   }
   __syncthreads();
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -368,7 +393,7 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
     for (int i = tid; i < r * r; i += blockDim.x) {
       double v = E[i] - (((i / r) == (i % r)) ? 1.0 : 0.0);
       E[i] = v;
-      em = fmax(em, fabs(v));
+      em = nanmax(em, fabs(v));
     }
     em = blk_max(em, red);
     if (em < 1e-4) break;
@@ -465,6 +490,7 @@ __device__ void finish_job(const DevProb& P, const Job& J, double* sm) {
       double tot = 0.0;
       for (int gg = 0; gg < groups; ++gg) tot += sm[gg * per + threadIdx.x];
       P.small[J.dst + i] = tot;
+      if (!isfinite(tot)) atomicOr(P.flags, 1u);   // an overflowed iterate ends the step as non-finite
     }
     __syncthreads();
   }

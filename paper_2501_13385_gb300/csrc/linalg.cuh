@@ -7,6 +7,9 @@
 #include "common.cuh"
 
 // Deterministic block-wide sum (fixed tree order); blockDim.x a power of two.
+// max that propagates NaN (fmax drops it): accuracy checks must fail on NaN
+__device__ __forceinline__ double nanmax(double a, double b) { return (a != a || b != b) ? (a + b) : fmax(a, b); }
+
 static __device__ double blk_sum(double v, double* sh) {
   __syncthreads();
   sh[threadIdx.x] = v;
@@ -184,11 +187,25 @@ static __device__ void blk_sym_eig(double* A, int n, double* V, double* w, doubl
 // One warp: lower Cholesky factor L of the SPD matrix A (FP64 input, n <= 32)
 // in FP32, and Li = L^{-1} (lower) in FP32.  L, Li: n*n floats (row-major).
 // Returns 1 if a pivot was not positive (it is then replaced by a tiny value).
-static __device__ int warp_chol_inv32(const double* A, int lda, int n, float* L, float* Li) {
+static __device__ int warp_chol_inv32(const double* A, int lda, int n, float* L, float* Li, int* pow2 = nullptr) {
   const int lane = threadIdx.x & 31;
+  // factor A 2^{-2k} (exact scaling, largest diagonal in [1/4, 4)) so FP32
+  // neither overflows nor underflows; with pow2 the caller gets k and the
+  // factors of A are L 2^k and Li 2^{-k}
+  int k2 = 0;
+  if (pow2) {
+    double dmax = 0.0;
+    for (int i = 0; i < n; ++i) dmax = fmax(dmax, fabs(A[i * lda + i]));
+    if (dmax > 0.0 && dmax <= 1.7e308) {
+      int e;
+      frexp(dmax, &e);
+      k2 = e / 2;
+    }
+    *pow2 = k2;
+  }
   for (int idx = lane; idx < n * n; idx += 32) {
     int i = idx / n, k = idx - (idx / n) * n;
-    L[idx] = (k <= i) ? (float)A[i * lda + k] : 0.f;
+    L[idx] = (k <= i) ? (float)ldexp(A[i * lda + k], -2 * k2) : 0.f;
   }
   __syncwarp();
   float scale = 0.f;
@@ -249,13 +266,14 @@ __device__ void warp_gemm(int M, int N, int K, const T* A, int lda, bool ta, con
 static __device__ double warp_spd_inverse(const double* A, int lda, int n, double* X, int ldx, float* L, float* Li,
                                           double* T) {
   const int lane = threadIdx.x & 31;
-  int bad = warp_chol_inv32(A, lda, n, L, Li);
+  int k2 = 0;
+  int bad = warp_chol_inv32(A, lda, n, L, Li, &k2);
   for (int idx = lane; idx < n * n; idx += 32) {
     int i = idx / n, j = idx - (idx / n) * n;
     int k0 = i > j ? i : j;
     double acc = 0.0;
     for (int k = k0; k < n; ++k) acc = fma((double)Li[k * n + i], (double)Li[k * n + j], acc);
-    X[i * ldx + j] = acc;
+    X[i * ldx + j] = ldexp(acc, -2 * k2);   // A^{-1} = 2^{-2k} (A 2^{-2k})^{-1}
   }
   __syncwarp();
   double* T1 = T;
@@ -266,8 +284,8 @@ static __device__ double warp_spd_inverse(const double* A, int lda, int n, doubl
     for (int i = lane; i < n; i += 32) T1[i * n + i] += 1.0;                          // T1 = I - A X
     __syncwarp();
     res = 0.0;
-    for (int idx = lane; idx < n * n; idx += 32) res = fmax(res, fabs(T1[idx]));
-    for (int o = 16; o > 0; o >>= 1) res = fmax(res, __shfl_xor_sync(0xffffffffu, res, o));
+    for (int idx = lane; idx < n * n; idx += 32) res = nanmax(res, fabs(T1[idx]));
+    for (int o = 16; o > 0; o >>= 1) res = nanmax(res, __shfl_xor_sync(0xffffffffu, res, o));
     if (!(res < 1.0)) break;                   // no contraction: leave it to the FP64 path
     if (it >= 2 && res < 1e-13) break;         // converged
     warp_gemm<double>(n, n, n, X, ldx, false, T1, n, false, T2, n, 1.0, false);      // T2 = X T1
@@ -286,7 +304,7 @@ static __device__ double blk_max(double v, double* sh) {
   sh[threadIdx.x] = v;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + s]);
+    if ((int)threadIdx.x < s) sh[threadIdx.x] = nanmax(sh[threadIdx.x], sh[threadIdx.x + s]);
     __syncthreads();
   }
   double out = sh[0];

@@ -121,6 +121,25 @@ def sample_linear_without_replacement(rng: Rng, total: int, count: int) -> np.nd
     return out
 
 
+def sample_multi_without_replacement(rng: Rng, n: Sequence[int], count: int) -> np.ndarray:
+    """`count` distinct multi-indices drawn uniformly coordinate by coordinate,
+    in draw order (first occurrence kept when a draw repeats): the sampler for
+    tensors whose entry count does not fit a linear index in double precision
+    (above 2^53 entries)."""
+    m = len(n)
+    nn = np.asarray(n, dtype=np.float64)
+    out = np.empty((0, m), dtype=np.int64)
+    while out.shape[0] < count:
+        need = count - out.shape[0]
+        rows = need + need // 4 + 16
+        u = rng.uniform(rows * m).reshape(rows, m)
+        cand = np.minimum(np.floor(u * nn).astype(np.int64), np.asarray(n, dtype=np.int64) - 1)
+        allv = np.concatenate([out, cand])
+        _, first = np.unique(allv, axis=0, return_index=True)
+        out = allv[np.sort(first)][:count]
+    return out.astype(np.int32)
+
+
 def linear_to_multi(lin: np.ndarray, n: Sequence[int]) -> np.ndarray:
     """Row-major mixed radix: x_1 is the most significant digit."""
     lin = np.asarray(lin, dtype=np.int64).copy()
@@ -238,8 +257,10 @@ def _perturbed_init(rng: Rng, truth, rel: float) -> List[np.ndarray]:
 def _finish(name, n, r, truth, rng, count, noise_std, noise_mode, init_rel, seed,
             truth_values=None):
     total = math.prod(n)
-    lin = sample_linear_without_replacement(rng, total, count)
-    idx = linear_to_multi(lin, n)
+    if total <= (1 << 53):
+        idx = linear_to_multi(sample_linear_without_replacement(rng, total, count), n)
+    else:
+        idx = sample_multi_without_replacement(rng, n, count)
     y = truth_values(idx) if truth_values is not None else _gather_values(truth, idx)
     if noise_std > 0.0:
         e = rng.normal(y.size)

@@ -255,3 +255,37 @@ def test_full_size_sampled_slices(maker):
                     assert np.all(np.abs(E - E_ref[x]) <= tol * (E_abs[x] + 1e-300) + 1e-300)
                     s = c.slice_energy(k)[x]
                     assert abs(s - (g @ g)) <= tol * ((g @ g) + 2 * np.abs(g) @ mag)
+
+
+def test_diverging_solve_never_reports_convergence():
+    # an absurd step scale makes the iteration diverge: the solver must end
+    # with TTC_ENOTCONV or TTC_ENONFINITE (a non-finite metric is never read
+    # as converged), whichever comes first
+    P = w.planted_small(6)
+    for rule in (ttc.STOP_RELERR, ttc.STOP_STEP):
+        with ctx_for(P, precision=ttc.PREC_FP64, alpha_scale=1e4, stop_rule=rule, tol=1e-6, max_iter=200) as c:
+            c.set_truth(P.truth)
+            try:
+                res = c.solve()
+            except ttc.TTCError as e:
+                assert e.status == -5
+            else:
+                assert not res["converged"] and res["status"] == "TTC_ENOTCONV"
+
+
+@pytest.mark.parametrize("e2", [-80, 72])
+def test_extreme_value_scales_fp64(e2):
+    # data scaled by 2^e2 (Grams far outside FP32's range): the FP32
+    # factorizations inside the dense stage scale exactly by powers of two, so
+    # the FP64 step still matches the oracle on the same scaled data
+    P = w.planted_small(2)
+    s = 2.0 ** e2
+    y = P.y * s
+    init = [c * 2.0 ** (e2 // 4) for c in P.init]
+    with ttc.Context(P.n, P.r, precision=ttc.PREC_FP64) as c:
+        c.set_observations(P.idx, y)
+        c.set_cores(init)
+        c.step()
+        got = c.get_cores()
+    ref, _ = o.prgd_step(init, P.idx, y, P.n, P.r, eps_rel=1.0, alpha_scale=1.5)
+    assert o.tt_dist(got, ref) <= 1e-10 * o.tt_norm(ref)

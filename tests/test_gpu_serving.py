@@ -140,3 +140,28 @@ def test_serving_poll_timeout_and_shutdown():
     assert r is None or r["status"] == "TTC_OK"
     t2 = submit(srv, 1)
     srv.close()   # finishes queued and running requests before returning
+
+
+def test_serving_mixed_stream_matches_solve_alone():
+    # requests of the mixed stream (orders 3-12, modes 4-256, ranks 2-16):
+    # different rank buckets and code widths share the engine
+    reqs = [w.random_request(2000 + i, max_entries=20_000) for i in range(6)]
+    opt = dict(precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_RESID, tol=1e-8, max_iter=40,
+               step_rule=ttc.STEP_STEEPEST)
+    alone = []
+    for Q in reqs:
+        with ttc.Context(Q.n, Q.r, options=ttc.default_options(**opt)) as c:
+            c.set_observations(Q.idx, Q.y)
+            c.set_cores(Q.init)
+            try:
+                alone.append((c.solve(), c.get_cores()))
+            except ttc.TTCError as e:          # a request may fail; the server must report the same
+                alone.append(({"status": ttc.STATUS[e.status]}, None))
+    with ttc.Server(max_slots=3) as srv:
+        tickets = [srv.submit(Q.n, Q.r, Q.idx, Q.y, Q.init, options=ttc.default_options(**opt)) for Q in reqs]
+        results = [srv.poll(t) for t in tickets]
+    for res, ref in zip(results, alone):
+        if ref[1] is None:
+            assert res["status"] == ref[0]["status"]
+        else:
+            check_same(res, ref)

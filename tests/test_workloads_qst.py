@@ -51,3 +51,13 @@ def test_qst_workload_shape_and_sampling():
     assert abs(P.N / 4 ** 10 - 0.0763) < 1e-3
     assert np.allclose(o.tt_eval(P.truth, P.idx), P.y, atol=1e-15)
     assert len(np.unique(P.idx.astype(np.int64) @ (4 ** np.arange(9, -1, -1)))) == P.N
+
+
+def test_huge_tensor_sampling_is_a_set_in_range():
+    # tensors with more than 2^53 entries are sampled coordinate by coordinate
+    n = [200] * 8
+    idx = w.sample_multi_without_replacement(w.Rng(5, 9), n, 5000)
+    assert idx.shape == (5000, 8) and idx.min() >= 0 and idx.max() < 200
+    assert len(np.unique(idx, axis=0)) == 5000
+    P = w.random_request(5)            # order 12, mode 148: about 1e26 entries
+    assert P.N == len(np.unique(P.idx, axis=0)) and np.all(P.idx < np.array(P.n))

@@ -86,9 +86,33 @@ struct BatchGroup {
   const int* seg_base;       // device [nprob + 1]: block offsets of the slice reduction
   const long long* tab_base; // device [nprob + 1]: row offsets of the interface tables
   int RC;                    // register size of the pass: the members' largest TT-rank
+  const int* pass_base_c[3]; // small ranks: block offsets per mode class (first, interior, last)
+  int pass_blocks_c[3];
   int pass_blocks, seg_blocks;
   long long tab_rows;
 };
+
+// mode classes of the small-rank sampled pass (separate launches, each at its
+// own register budget): the first mode, the interior modes, the last mode;
+// PC_ALL is the large-rank pass over all chunks
+enum { PC_FIRST = 0, PC_MIDDLE = 1, PC_LAST = 2, PC_ALL = 3 };
+inline void ttc_pass_class_range(const DevProb& P, int cls, int* c0, int* c1) {
+  if (cls == PC_FIRST) {
+    *c0 = 0;
+    *c1 = P.chunk_base[1];
+  } else if (cls == PC_LAST) {
+    *c0 = P.chunk_base[P.m - 1];
+    *c1 = P.chunk_base[P.m];
+  } else {
+    *c0 = P.chunk_base[1];
+    *c1 = P.chunk_base[P.m - 1];
+  }
+}
+inline int ttc_pass_class_blocks(const DevProb& P, int cls) {
+  int c0, c1;
+  ttc_pass_class_range(P, cls, &c0, &c1);
+  return c1 > c0 ? (c1 - c0 + TTC_NT / 32 - 1) / (TTC_NT / 32) : 0;
+}
 
 // blocks of one sampled pass: small rank buckets (R <= 8) reduce one chunk
 // per warp, larger ones one chunk per block
@@ -108,6 +132,8 @@ struct PassLaunch {
 // RC = the largest TT-rank (1..8); pass_large.cu: buckets 16 and 32
 int ttc_pass_small_f32(int RC, const PassLaunch& L);
 int ttc_pass_small_f64(int RC, const PassLaunch& L);
+int ttc_pass_small_f32_r4(int RC, const PassLaunch& L);   // pass_small_f32_r4.cu: RC = 1..4
+int ttc_pass_small_f64_r4(int RC, const PassLaunch& L);   // pass_small_f64_r4.cu
 int ttc_pass_large(bool f32, int R, const PassLaunch& L);
 int ttc_pass_opt_in_large();
 

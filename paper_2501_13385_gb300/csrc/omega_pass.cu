@@ -205,7 +205,12 @@ int launch_pass(ttc_ctx* c, int RC) {
   const int nsegb = ttc_seg_blocks(P);
   k_segment_reduce<T><<<nsegb, kSegThreads, 0, c->stream>>>(P, nsegb);
   TTC_CUDA(cudaGetLastError());
-  c->nlaunch += 2;
+  int passes = 1;
+  if (R <= 8) {   // one launch per non-empty mode class
+    passes = 0;
+    for (int cls = 0; cls < 3; ++cls) passes += ttc_pass_class_blocks(P, cls) > 0 ? 1 : 0;
+  }
+  c->nlaunch += 1 + passes;
   return TTC_OK;
 }
 

@@ -489,12 +489,13 @@ __device__ __forceinline__ void warp_chunk_rows(const DevProb& P, int k, int beg
 }
 
 // Any other chunk: interfaces through tables and chains of core slices, with
-// loops that stop at the runtime ranks.
-template <typename T, int R, int RC>
+// loops that stop at the runtime ranks.  KIND shapes the accumulators as in
+// warp_chunk_rows (0: first mode, 1: last mode, 2: interior).
+template <typename T, int R, int RC, int KIND>
 __device__ __forceinline__ void warp_chunk_general(const DevProb& P, int k, int beg, int end, const T* Ts, T* out) {
   const int lane = threadIdx.x & 31;
   const int ra = P.r[k], rb = P.r[k + 1];
-  constexpr int NV = pow2_at_least(RC * RC);
+  constexpr int NV = pow2_at_least(KIND == 2 ? RC * RC : RC);
   T acc[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) acc[i] = 0;
@@ -518,20 +519,34 @@ __device__ __forceinline__ void warp_chunk_general(const DevProb& P, int k, int 
     const T g = interfaces<T, R, RC>(P, k, words, Ts, lv, rv) - yv;
     if (keep) P.g[P.perm[0][e]] = (double)g;
     s2 = fma(g, g, s2);
-#pragma unroll
-    for (int a = 0; a < RC; ++a) {
-      if (a >= ra) break;
-      const T gl = g * lv[a];
+    if constexpr (KIND == 0) {
 #pragma unroll
       for (int b = 0; b < RC; ++b) {
         if (b >= rb) break;
-        acc[a * RC + b] = fma(gl, rv[b], acc[a * RC + b]);
+        acc[b] = fma(g, rv[b], acc[b]);
+      }
+    } else if constexpr (KIND == 1) {
+#pragma unroll
+      for (int a = 0; a < RC; ++a) {
+        if (a >= ra) break;
+        acc[a] = fma(g, lv[a], acc[a]);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < RC; ++a) {
+        if (a >= ra) break;
+        const T gl = g * lv[a];
+#pragma unroll
+        for (int b = 0; b < RC; ++b) {
+          if (b >= rb) break;
+          acc[a * RC + b] = fma(gl, rv[b], acc[a * RC + b]);
+        }
       }
     }
   }
   s2 = warp_sum(s2);
   if (lane == 0) out[0] = s2;
-  store_partials<T, NV, 2, RC>(acc, lane, out, ra, rb);
+  store_partials<T, NV, KIND, RC>(acc, lane, out, ra, rb);
 }
 
 // Small ranks (R <= 8): one warp reduces one chunk of at most TTC_CHUNK
@@ -540,10 +555,17 @@ __device__ __forceinline__ void warp_chunk_general(const DevProb& P, int k, int 
 // processed), forms its interfaces and residual, and accumulates the
 // rank-one terms g * l_{k-1} r_{k+1}^T and g^2 in registers; a butterfly then
 // sums the lanes.  No shared memory beyond the slice, no block barriers.
-template <typename T, int R, int RC>
+template <typename T, int R, int RC, int MC>
 __device__ __forceinline__ void sample_project_warp(const DevProb& P, const int call, T* Ts) {
   int k = 0;
-  while (k + 1 < P.m && call >= P.chunk_base[k + 1]) ++k;
+  if constexpr (MC == PC_FIRST) {
+    k = 0;
+  } else if constexpr (MC == PC_LAST) {
+    k = P.m - 1;
+  } else {
+    k = 1;
+    while (k + 2 < P.m && call >= P.chunk_base[k + 1]) ++k;
+  }
   const int c = call - P.chunk_base[k];
   const int x = P.cseg[k][c];
   const int beg = P.seg[k][x] + (c - P.cfirst[k][x]) * TTC_CHUNK;
@@ -560,19 +582,14 @@ __device__ __forceinline__ void sample_project_warp(const DevProb& P, const int 
   __syncwarp();
   T* out = reinterpret_cast<T*>(P.part) + (long long)(P.chunk_base[k] + c) * P.part_stride;
   RowSrc<T> ls{}, rs{};
-  const bool lrow = (k == 0) || left_src<T>(P, k, ls);
-  const bool rrow = (k == P.m - 1) || right_src<T>(P, k, rs);
   constexpr int U = sizeof(T) == 4 ? 2 : 1;   // FP64 is bound by its FMA rate
-  if (lrow && rrow) {
-    if (k == 0)
-      warp_chunk_rows<T, R, RC, 0, U>(P, k, beg, end, Ts, ls, rs, out);
-    else if (k == P.m - 1)
-      warp_chunk_rows<T, R, RC, 1, U>(P, k, beg, end, Ts, ls, rs, out);
-    else
-      warp_chunk_rows<T, R, RC, 2, U>(P, k, beg, end, Ts, ls, rs, out);
-  } else {
-    warp_chunk_general<T, R, RC>(P, k, beg, end, Ts, out);
-  }
+  constexpr int KIND = MC == PC_FIRST ? 0 : MC == PC_LAST ? 1 : 2;
+  const bool lrow = (KIND == 0) || left_src<T>(P, k, ls);
+  const bool rrow = (KIND == 1) || right_src<T>(P, k, rs);
+  if (lrow && rrow)
+    warp_chunk_rows<T, R, RC, KIND, U>(P, k, beg, end, Ts, ls, rs, out);
+  else
+    warp_chunk_general<T, R, RC, KIND>(P, k, beg, end, Ts, out);
 }
 
 // Large ranks (R >= 16): one block reduces one chunk.  The rank-one terms of
@@ -664,29 +681,48 @@ __device__ __forceinline__ void sample_project_block(const DevProb& P, const int
     }
 }
 
-template <typename T, int R, int RC>
+// chunks [c0, c1) of a mode class (small ranks; see ttc_pass_class_range)
+__device__ __forceinline__ void class_range(const DevProb& P, int mc, int& c0, int& c1) {
+  if (mc == PC_FIRST) {
+    c0 = 0;
+    c1 = P.chunk_base[1];
+  } else if (mc == PC_LAST) {
+    c0 = P.chunk_base[P.m - 1];
+    c1 = P.chunk_base[P.m];
+  } else {
+    c0 = P.chunk_base[1];
+    c1 = P.chunk_base[P.m - 1];
+  }
+}
+
+// MC: a mode class (small ranks, one chunk per warp) or PC_ALL (large ranks,
+// one chunk per block over all modes)
+template <typename T, int R, int RC, int MC>
 __device__ __forceinline__ void sample_project(const DevProb& P, const int blk) {
-  if constexpr (R <= 8) {
+  if constexpr (MC != PC_ALL) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int warp = threadIdx.x >> 5;
-    const int call = blk * kWarps + warp;
-    if (call >= P.chunk_base[P.m]) return;
-    sample_project_warp<T, R, RC>(P, call, reinterpret_cast<T*>(smraw) + warp * R * R);
+    int c0, c1;
+    class_range(P, MC, c0, c1);
+    const int call = c0 + blk * kWarps + warp;
+    if (call >= c1) return;
+    sample_project_warp<T, R, RC, MC>(P, call, reinterpret_cast<T*>(smraw) + warp * R * R);
   } else {
     sample_project_block<T, R>(P, blk);
   }
 }
 
-// resident blocks per SM the register budget is sized for: small FP32 ranks
-// keep two 256-thread blocks (16 warps, two gathers in flight each)
-template <typename T, int RC>
+// resident blocks per SM the register budget is sized for: FP32 first/last
+// modes (one gather per entry, r accumulators) keep four 256-thread blocks,
+// small FP32 interior ranks two (16 warps, two gathers in flight each)
+template <typename T, int RC, int MC>
 constexpr int min_blocks() {
-  return (sizeof(T) == 4 && RC <= 5) ? 2 : 1;
+  return sizeof(T) != 4 ? 1 : (MC == PC_FIRST || MC == PC_LAST) ? (RC <= 6 ? 4 : 3) : (MC == PC_MIDDLE && RC <= 5) ? 2 : 1;
 }
 
-template <typename T, int R, int RC>
-__global__ void __launch_bounds__(TTC_NT, (min_blocks<T, RC>())) k_sample_project(const DevProb P) {
-  sample_project<T, R, RC>(P, blockIdx.x);
+template <typename T, int R, int RC, int MC>
+__global__ void __launch_bounds__(TTC_NT, (min_blocks<T, RC, MC>())) k_sample_project(const DevProb P) {
+  sample_project<T, R, RC, MC>(P, blockIdx.x);
 }
 
 // batched form: one launch covers every problem of a batch; blocks
@@ -709,13 +745,13 @@ __device__ __forceinline__ void stage_desc(const DevProb* __restrict__ src, DevP
   __syncthreads();
 }
 
-template <typename T, int R, int RC>
-__global__ void __launch_bounds__(TTC_NT, (min_blocks<T, RC>())) k_sample_project_batch(const DevProb* __restrict__ probs,
-                                                                  const int* __restrict__ base, int nprob) {
+template <typename T, int R, int RC, int MC>
+__global__ void __launch_bounds__(TTC_NT, (min_blocks<T, RC, MC>())) k_sample_project_batch(
+    const DevProb* __restrict__ probs, const int* __restrict__ base, int nprob) {
   __shared__ __align__(16) DevProb Ps;
   const int p = find_problem(base, nprob, blockIdx.x);
   stage_desc(probs + p, &Ps);
-  sample_project<T, R, RC>(Ps, blockIdx.x - __ldg(base + p));
+  sample_project<T, R, RC, MC>(Ps, blockIdx.x - __ldg(base + p));
 }
 
 template <typename T>
@@ -724,15 +760,37 @@ inline size_t pass_smem(int R) {
   return sizeof(T) * (size_t)(R * R + 2 * TTC_NT * R);
 }
 
-// one launch of the pass kernel: a single problem (g == nullptr) or a batch group
+// the pass of a single problem (g == nullptr) or a batch group: small ranks
+// as one launch per mode class (first, interior, last), large ranks as one
+// launch over all chunks
 template <typename T, int R, int RC>
 int launch(const PassLaunch& L) {
   const size_t smem = pass_smem<T>(R);
-  if (L.g)
-    k_sample_project_batch<T, R, RC><<<L.g->pass_blocks, TTC_NT, smem, L.st>>>(L.g->probs, L.g->pass_base,
-                                                                                 L.g->nprob);
-  else
-    k_sample_project<T, R, RC><<<ttc_pass_blocks(*L.P, R), TTC_NT, smem, L.st>>>(*L.P);
+  if constexpr (R <= 8) {
+    if (L.g) {
+      if (L.g->pass_blocks_c[PC_FIRST] > 0)
+        k_sample_project_batch<T, R, RC, PC_FIRST><<<L.g->pass_blocks_c[PC_FIRST], TTC_NT, smem, L.st>>>(
+            L.g->probs, L.g->pass_base_c[PC_FIRST], L.g->nprob);
+      if (L.g->pass_blocks_c[PC_MIDDLE] > 0)
+        k_sample_project_batch<T, R, RC, PC_MIDDLE><<<L.g->pass_blocks_c[PC_MIDDLE], TTC_NT, smem, L.st>>>(
+            L.g->probs, L.g->pass_base_c[PC_MIDDLE], L.g->nprob);
+      if (L.g->pass_blocks_c[PC_LAST] > 0)
+        k_sample_project_batch<T, R, RC, PC_LAST><<<L.g->pass_blocks_c[PC_LAST], TTC_NT, smem, L.st>>>(
+            L.g->probs, L.g->pass_base_c[PC_LAST], L.g->nprob);
+    } else {
+      const int b0 = ttc_pass_class_blocks(*L.P, PC_FIRST), b1 = ttc_pass_class_blocks(*L.P, PC_MIDDLE),
+                b2 = ttc_pass_class_blocks(*L.P, PC_LAST);
+      if (b0 > 0) k_sample_project<T, R, RC, PC_FIRST><<<b0, TTC_NT, smem, L.st>>>(*L.P);
+      if (b1 > 0) k_sample_project<T, R, RC, PC_MIDDLE><<<b1, TTC_NT, smem, L.st>>>(*L.P);
+      if (b2 > 0) k_sample_project<T, R, RC, PC_LAST><<<b2, TTC_NT, smem, L.st>>>(*L.P);
+    }
+  } else {
+    if (L.g)
+      k_sample_project_batch<T, R, RC, PC_ALL><<<L.g->pass_blocks, TTC_NT, smem, L.st>>>(L.g->probs, L.g->pass_base,
+                                                                                          L.g->nprob);
+    else
+      k_sample_project<T, R, RC, PC_ALL><<<ttc_pass_blocks(*L.P, R), TTC_NT, smem, L.st>>>(*L.P);
+  }
   TTC_CUDA(cudaGetLastError());
   return TTC_OK;
 }
@@ -741,10 +799,10 @@ template <typename T, int R, int RC>
 int opt_in() {
   const size_t smem = pass_smem<T>(R);
   if (smem > 48 * 1024) {
-    TTC_CUDA(cudaFuncSetAttribute(k_sample_project<T, R, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    TTC_CUDA(cudaFuncSetAttribute(k_sample_project<T, R, RC, PC_ALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
-    TTC_CUDA(cudaFuncSetAttribute(k_sample_project_batch<T, R, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    TTC_CUDA(cudaFuncSetAttribute(k_sample_project_batch<T, R, RC, PC_ALL>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   }
   return TTC_OK;
 }

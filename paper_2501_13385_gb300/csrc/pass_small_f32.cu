@@ -1,18 +1,15 @@
-// FP32 sampled pass for rank buckets 4 and 8: one kernel per register size
-// RC = 1..8 (the problem's largest TT-rank), single-problem and batched.
+// FP32 sampled pass for rank bucket 8: kernels per register size RC = 5..8
+// (the problem's largest TT-rank) and mode class, single-problem and batched;
+// RC = 1..4 (bucket 4) live in pass_small_f32_r4.cu.
 #include "omega_pass.cuh"
 
 int ttc_pass_small_f32(int RC, const PassLaunch& L) {
   using namespace ttc_pass;
   switch (RC) {
-    case 1: return launch<float, 4, 1>(L);
-    case 2: return launch<float, 4, 2>(L);
-    case 3: return launch<float, 4, 3>(L);
-    case 4: return launch<float, 4, 4>(L);
     case 5: return launch<float, 8, 5>(L);
     case 6: return launch<float, 8, 6>(L);
     case 7: return launch<float, 8, 7>(L);
     case 8: return launch<float, 8, 8>(L);
-    default: return TTC_EUNSUPPORTED;
+    default: return ttc_pass_small_f32_r4(RC, L);
   }
 }

@@ -1,0 +1,14 @@
+// FP32 sampled pass for rank bucket 4: kernels per register size RC = 1..4
+// and mode class, single-problem and batched.
+#include "omega_pass.cuh"
+
+int ttc_pass_small_f32_r4(int RC, const PassLaunch& L) {
+  using namespace ttc_pass;
+  switch (RC) {
+    case 1: return launch<float, 4, 1>(L);
+    case 2: return launch<float, 4, 2>(L);
+    case 3: return launch<float, 4, 3>(L);
+    case 4: return launch<float, 4, 4>(L);
+    default: return TTC_EUNSUPPORTED;
+  }
+}

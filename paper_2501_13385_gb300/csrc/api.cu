@@ -16,6 +16,26 @@ void ttc_record_cuda_error(cudaError_t e) {
   snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
+int ttc_fork_create(PassFork& f) {
+  for (int i = 0; i < 2; ++i) {
+    TTC_CUDA(cudaStreamCreateWithFlags(&f.aux[i], cudaStreamNonBlocking));
+    TTC_CUDA(cudaEventCreateWithFlags(&f.join[i], cudaEventDisableTiming));
+  }
+  TTC_CUDA(cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming));
+  return TTC_OK;
+}
+
+void ttc_fork_destroy(PassFork& f) {
+  for (int i = 0; i < 2; ++i) {
+    if (f.aux[i]) cudaStreamDestroy(f.aux[i]);
+    if (f.join[i]) cudaEventDestroy(f.join[i]);
+    f.aux[i] = nullptr;
+    f.join[i] = nullptr;
+  }
+  if (f.fork) cudaEventDestroy(f.fork);
+  f.fork = nullptr;
+}
+
 int ttc_alloc(ttc_ctx* c, void** p, size_t bytes, bool obs) {
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
@@ -256,6 +276,7 @@ int ttc_create(ttc_ctx** out, int d, const int64_t* n, const int32_t* r, const t
     if ((s = ttc_alloc(c, (void**)&P.s[k], sizeof(double) * (size_t)n[k], false)) != TTC_OK) break;
     if ((s = ttc_alloc(c, (void**)&P.E[k], sizeof(double) * cnt, false)) != TTC_OK) break;
   }
+  if (s == TTC_OK) s = ttc_fork_create(c->fork);
   if (s == TTC_OK) s = ttc_prepare_omega_pass();
   if (s == TTC_OK) s = ttc_alloc_dense(c);
   if (s == TTC_OK) {
@@ -281,6 +302,7 @@ void ttc_destroy(ttc_ctx* c) {
   drop_graphs(c);
   if (c->ev_beg) cudaEventDestroy(c->ev_beg);
   if (c->ev_end) cudaEventDestroy(c->ev_end);
+  ttc_fork_destroy(c->fork);
   ttc_free_obs(c);
   for (auto& b : c->bufs) cudaFree(b.p);
   c->bufs.clear();

@@ -18,6 +18,7 @@ struct ttc_batch {
   std::vector<int> prec_at_capture;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  PassFork pfork;              // concurrent mode-class launches of the batched pass
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> joins;
   struct Group {
@@ -139,7 +140,7 @@ int capture(ttc_batch* b) {
   if (b->prof) e = cudaEventRecordWithFlags(b->ev_beg, b->stream, cudaEventRecordExternal);
   for (auto& G : b->groups)
     if (s == TTC_OK && e == cudaSuccess) {
-      s = ttc_launch_omega_pass_batch(G.g, b->stream, 0);
+      s = ttc_launch_omega_pass_batch(G.g, b->stream, 0, &b->pfork);
       if (G.g.R <= 8)   // one launch per non-empty mode class
         for (int cls = 0; cls < 3; ++cls) batched += G.g.pass_blocks_c[cls] > 0 ? 1 : 0;
       else
@@ -212,6 +213,7 @@ int ttc_batch_create(ttc_batch** out, ttc_ctx* const* members, int count, void* 
     e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     b->own_stream = (e == cudaSuccess);
   }
+  if (e == cudaSuccess && ttc_fork_create(b->pfork) != TTC_OK) e = cudaErrorMemoryAllocation;
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   b->joins.assign(count, nullptr);
   for (int i = 0; i < count && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming);
@@ -304,6 +306,7 @@ void ttc_batch_destroy(ttc_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   free_groups(b);
   if (b->fork) cudaEventDestroy(b->fork);
+  ttc_fork_destroy(b->pfork);
   for (auto ev : b->joins)
     if (ev) cudaEventDestroy(ev);
   if (b->ev_beg) cudaEventDestroy(b->ev_beg);

@@ -12,6 +12,17 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// streams and events that let the mode-class launches of one pass run
+// concurrently (forked from and joined back into the issuing stream; inside
+// a stream capture they become parallel graph branches)
+struct PassFork {
+  cudaStream_t aux[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[2] = {nullptr, nullptr};
+};
+int ttc_fork_create(PassFork& f);
+void ttc_fork_destroy(PassFork& f);
+
 struct ttc_ctx {
   int m = 0;
   long long n[TTC_MAXM] = {0};
@@ -51,6 +62,7 @@ struct ttc_ctx {
   int cur_prec = TTC_PREC_FP64;    // precision of the Omega pass for the next step
   double alpha_ovr = 0.0;           // step-size override currently on the device
   double ynorm2 = 0.0;              // ||y||^2 of the observations
+  PassFork fork;                    // concurrent mode-class launches of the sampled pass
 };
 
 // the solver's per-iteration bookkeeping (shared by ttc_solve and the server)
@@ -127,6 +139,7 @@ struct PassLaunch {
   const DevProb* P;
   const BatchGroup* g;
   cudaStream_t st;
+  const PassFork* fork;      // may be null: the class launches then run in sequence
 };
 // pass_small_f32.cu / pass_small_f64.cu: rank buckets 4 and 8, register size
 // RC = the largest TT-rank (1..8); pass_large.cu: buckets 16 and 32
@@ -145,7 +158,8 @@ inline int ttc_seg_blocks(const DevProb& P) {
 }
 
 // omega_pass.cu
-int ttc_launch_omega_pass_batch(const BatchGroup& g, cudaStream_t st, int phase);   // 0: pass, 1: slice reduction, 2: tables
+// phase 0: pass (mode classes forked onto `fork`'s streams when given), 1: slice reduction, 2: tables
+int ttc_launch_omega_pass_batch(const BatchGroup& g, cudaStream_t st, int phase, const PassFork* fork = nullptr);
 void ttc_plan_tables(ttc_ctx* c);
 int ttc_prepare_omega_pass();
 int ttc_launch_omega_pass(ttc_ctx* c, int prec);

@@ -199,7 +199,7 @@ int launch_pass(ttc_ctx* c, int RC) {
     if (cs == cudaStreamCaptureStatusActive) evflags = cudaEventRecordExternal;
     TTC_CUDA(cudaEventRecordWithFlags(c->ev_beg, c->stream, evflags));
   }
-  PassLaunch L{&P, nullptr, c->stream};
+  PassLaunch L{&P, nullptr, c->stream, &c->fork};
   TTC_TRY(launch_pass_kernel(sizeof(T) == 4, R, RC, L));
   if (c->prof) TTC_CUDA(cudaEventRecordWithFlags(c->ev_end, c->stream, evflags));
   const int nsegb = ttc_seg_blocks(P);
@@ -223,12 +223,12 @@ int launch_eval(ttc_ctx* c, const int32_t* idx_dev, long long M, double* out_dev
 }
 
 template <typename T, int R>
-int launch_pass_batch(const BatchGroup& g, cudaStream_t st, int phase) {
+int launch_pass_batch(const BatchGroup& g, cudaStream_t st, int phase, const PassFork* fork) {
   if (phase == 2) {
     if (g.tab_rows > 0)
       k_build_tables_batch<T, R><<<table_blocks(g.tab_rows), 256, 0, st>>>(g.probs, g.tab_base, g.nprob, g.tab_rows);
   } else if (phase == 0) {
-    PassLaunch L{nullptr, &g, st};
+    PassLaunch L{nullptr, &g, st, fork};
     return launch_pass_kernel(sizeof(T) == 4, R, g.RC, L);
   } else {
     k_segment_reduce_batch<T><<<g.seg_blocks, kSegThreads, 0, st>>>(g.probs, g.seg_base, g.nprob);
@@ -242,13 +242,13 @@ int launch_pass_batch(const BatchGroup& g, cudaStream_t st, int phase) {
 // one-time kernel attributes (outside any stream capture)
 int ttc_prepare_omega_pass() { return ttc_pass_opt_in_large(); }
 
-int ttc_launch_omega_pass_batch(const BatchGroup& g, cudaStream_t st, int phase) {
+int ttc_launch_omega_pass_batch(const BatchGroup& g, cudaStream_t st, int phase, const PassFork* fork) {
   const bool f32 = (g.prec != TTC_PREC_FP64);
   switch (g.R) {
-    case 4: return f32 ? launch_pass_batch<float, 4>(g, st, phase) : launch_pass_batch<double, 4>(g, st, phase);
-    case 8: return f32 ? launch_pass_batch<float, 8>(g, st, phase) : launch_pass_batch<double, 8>(g, st, phase);
-    case 16: return f32 ? launch_pass_batch<float, 16>(g, st, phase) : launch_pass_batch<double, 16>(g, st, phase);
-    default: return f32 ? launch_pass_batch<float, 32>(g, st, phase) : launch_pass_batch<double, 32>(g, st, phase);
+    case 4: return f32 ? launch_pass_batch<float, 4>(g, st, phase, fork) : launch_pass_batch<double, 4>(g, st, phase, fork);
+    case 8: return f32 ? launch_pass_batch<float, 8>(g, st, phase, fork) : launch_pass_batch<double, 8>(g, st, phase, fork);
+    case 16: return f32 ? launch_pass_batch<float, 16>(g, st, phase, fork) : launch_pass_batch<double, 16>(g, st, phase, fork);
+    default: return f32 ? launch_pass_batch<float, 32>(g, st, phase, fork) : launch_pass_batch<double, 32>(g, st, phase, fork);
   }
 }
 

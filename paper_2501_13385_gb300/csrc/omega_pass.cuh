@@ -116,6 +116,82 @@ __device__ __forceinline__ void load_row(const double* __restrict__ row, int len
   }
 }
 
+// L2 eviction policies: the streamed codes and values are read once per pass
+// (evict first, no L1 allocation), the interface rows are gathered many times
+// (evict last), so the stream does not push the tables out of L2
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p, uint64_t pol) {
+  uint32_t v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_stream(const float* p, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double ld_stream(const double* p, uint64_t pol) {
+  double v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
+// load_row for gathered interface rows, with an L2 policy (rows padded and
+// aligned as for load_row)
+template <int RC>
+__device__ __forceinline__ void load_row_hint(const float* row, int len, float (&out)[RC], uint64_t pol) {
+  if constexpr (RC > 4) {
+#pragma unroll
+    for (int b = 0; b < RC; b += 8) {
+      if (b >= len) break;
+      float v[8];
+      asm("ld.global.nc.L2::cache_hint.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+          : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+          : "l"(row + b), "l"(pol));
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (b + i < RC) out[b + i] = v[i];
+    }
+  } else {
+    float v[4];
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+        : "l"(row), "l"(pol));
+#pragma unroll
+    for (int i = 0; i < RC; ++i) out[i] = v[i];
+  }
+}
+template <int RC>
+__device__ __forceinline__ void load_row_hint(const double* row, int len, double (&out)[RC], uint64_t pol) {
+  if constexpr (RC > 2) {
+#pragma unroll
+    for (int b = 0; b < RC; b += 4) {
+      if (b >= len) break;
+      double v[4];
+      asm("ld.global.nc.L2::cache_hint.v4.f64 {%0,%1,%2,%3}, [%4], %5;"
+          : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+          : "l"(row + b), "l"(pol));
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (b + i < RC) out[b + i] = v[i];
+    }
+  } else {
+    double v[2];
+    asm("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;" : "=d"(v[0]), "=d"(v[1]) : "l"(row), "l"(pol));
+#pragma unroll
+    for (int i = 0; i < RC; ++i) out[i] = v[i];
+  }
+}
+
 template <typename T, int RC>
 __device__ __forceinline__ void zero(T (&v)[RC]) {
 #pragma unroll
@@ -369,13 +445,13 @@ __device__ __forceinline__ const float* y_ptr<float>(const DevProb& P, int k) { 
 template <>
 __device__ __forceinline__ const double* y_ptr<double>(const DevProb& P, int k) { return P.y64[k]; }
 
-__device__ __forceinline__ Code load_code_at(const uint32_t* __restrict__ p, int W, int e) {
+__device__ __forceinline__ Code load_code_at(const uint32_t* __restrict__ p, int W, int e, uint64_t pol) {
   Code c;
   p += (long long)e * W;
-  c.w0 = __ldg(p);
-  c.w1 = W > 1 ? __ldg(p + 1) : 0u;
-  c.w2 = W > 2 ? __ldg(p + 2) : 0u;
-  c.w3 = W > 3 ? __ldg(p + 3) : 0u;
+  c.w0 = ld_stream(p, pol);
+  c.w1 = W > 1 ? ld_stream(p + 1, pol) : 0u;
+  c.w2 = W > 2 ? ld_stream(p + 2, pol) : 0u;
+  c.w3 = W > 3 ? ld_stream(p + 3, pol) : 0u;
   return c;
 }
 
@@ -397,6 +473,7 @@ __device__ __forceinline__ void warp_chunk_rows(const DevProb& P, int k, int beg
   const bool keep = P.keep_residual && k == 0;
   double* __restrict__ gout = P.g;
   const int* __restrict__ perm0 = P.perm[0];
+  const uint64_t pol_stream = policy_evict_first(), pol_rows = policy_evict_last();
   constexpr int NV = pow2_at_least(KIND == 2 ? RC * RC : RC);
   T acc[NV];
 #pragma unroll
@@ -417,8 +494,8 @@ __device__ __forceinline__ void warp_chunk_rows(const DevProb& P, int k, int beg
     nw[u] = {0u, 0u, 0u, 0u};
     ny[u] = 0;
     if (eu < end) {
-      nw[u] = load_code_at(code, W, eu);
-      ny[u] = __ldg(yk + eu);
+      nw[u] = load_code_at(code, W, eu, pol_stream);
+      ny[u] = ld_stream(yk + eu, pol_stream);
     }
   }
   for (int e = beg + lane; e < end; e += 32 * U) {
@@ -430,8 +507,8 @@ __device__ __forceinline__ void warp_chunk_rows(const DevProb& P, int k, int beg
       yv[u] = ny[u];
       const int en = e + 32 * (U + u);
       if (en < end) {
-        nw[u] = load_code_at(code, W, en);
-        ny[u] = __ldg(yk + en);
+        nw[u] = load_code_at(code, W, en, pol_stream);
+        ny[u] = ld_stream(yk + en, pol_stream);
       }
     }
     T lv[U][RC], rv[U][RC];
@@ -439,8 +516,8 @@ __device__ __forceinline__ void warp_chunk_rows(const DevProb& P, int k, int beg
     for (int u = 0; u < U; ++u) {
       zero(lv[u]);
       zero(rv[u]);
-      if constexpr (KIND != 0) load_row<RC, true>(row_of(ls, w[u]), RC, lv[u]);
-      if constexpr (KIND != 1) load_row<RC, true>(row_of(rs, w[u]), RC, rv[u]);
+      if constexpr (KIND != 0) load_row_hint<RC>(row_of(ls, w[u]), RC, lv[u], pol_rows);
+      if constexpr (KIND != 1) load_row_hint<RC>(row_of(rs, w[u]), RC, rv[u], pol_rows);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -767,22 +844,39 @@ template <typename T, int R, int RC>
 int launch(const PassLaunch& L) {
   const size_t smem = pass_smem<T>(R);
   if constexpr (R <= 8) {
+    // the interior class on the issuing stream, the first and last classes
+    // on the fork's streams (when given), joined back before returning
+    cudaStream_t sf = L.st, sl = L.st;
+    if (L.fork) {
+      TTC_CUDA(cudaEventRecord(L.fork->fork, L.st));
+      TTC_CUDA(cudaStreamWaitEvent(L.fork->aux[0], L.fork->fork, 0));
+      TTC_CUDA(cudaStreamWaitEvent(L.fork->aux[1], L.fork->fork, 0));
+      sf = L.fork->aux[0];
+      sl = L.fork->aux[1];
+    }
     if (L.g) {
       if (L.g->pass_blocks_c[PC_FIRST] > 0)
-        k_sample_project_batch<T, R, RC, PC_FIRST><<<L.g->pass_blocks_c[PC_FIRST], TTC_NT, smem, L.st>>>(
+        k_sample_project_batch<T, R, RC, PC_FIRST><<<L.g->pass_blocks_c[PC_FIRST], TTC_NT, smem, sf>>>(
             L.g->probs, L.g->pass_base_c[PC_FIRST], L.g->nprob);
       if (L.g->pass_blocks_c[PC_MIDDLE] > 0)
         k_sample_project_batch<T, R, RC, PC_MIDDLE><<<L.g->pass_blocks_c[PC_MIDDLE], TTC_NT, smem, L.st>>>(
             L.g->probs, L.g->pass_base_c[PC_MIDDLE], L.g->nprob);
       if (L.g->pass_blocks_c[PC_LAST] > 0)
-        k_sample_project_batch<T, R, RC, PC_LAST><<<L.g->pass_blocks_c[PC_LAST], TTC_NT, smem, L.st>>>(
+        k_sample_project_batch<T, R, RC, PC_LAST><<<L.g->pass_blocks_c[PC_LAST], TTC_NT, smem, sl>>>(
             L.g->probs, L.g->pass_base_c[PC_LAST], L.g->nprob);
     } else {
       const int b0 = ttc_pass_class_blocks(*L.P, PC_FIRST), b1 = ttc_pass_class_blocks(*L.P, PC_MIDDLE),
                 b2 = ttc_pass_class_blocks(*L.P, PC_LAST);
-      if (b0 > 0) k_sample_project<T, R, RC, PC_FIRST><<<b0, TTC_NT, smem, L.st>>>(*L.P);
+      if (b0 > 0) k_sample_project<T, R, RC, PC_FIRST><<<b0, TTC_NT, smem, sf>>>(*L.P);
       if (b1 > 0) k_sample_project<T, R, RC, PC_MIDDLE><<<b1, TTC_NT, smem, L.st>>>(*L.P);
-      if (b2 > 0) k_sample_project<T, R, RC, PC_LAST><<<b2, TTC_NT, smem, L.st>>>(*L.P);
+      if (b2 > 0) k_sample_project<T, R, RC, PC_LAST><<<b2, TTC_NT, smem, sl>>>(*L.P);
+    }
+    TTC_CUDA(cudaGetLastError());
+    if (L.fork) {
+      TTC_CUDA(cudaEventRecord(L.fork->join[0], sf));
+      TTC_CUDA(cudaEventRecord(L.fork->join[1], sl));
+      TTC_CUDA(cudaStreamWaitEvent(L.st, L.fork->join[0], 0));
+      TTC_CUDA(cudaStreamWaitEvent(L.st, L.fork->join[1], 0));
     }
   } else {
     if (L.g)

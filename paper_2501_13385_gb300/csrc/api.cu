@@ -3,6 +3,8 @@
 // sequence captured once into a CUDA graph per precision, the solver loop
 // and read-back of intermediate results.
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -36,9 +38,48 @@ void ttc_fork_destroy(PassFork& f) {
   f.fork = nullptr;
 }
 
+// The library's device memory pool (one per device): stream-ordered
+// allocations that stay cached after they are freed (release threshold at
+// its maximum), so contexts and layouts built again and again (serving,
+// end-to-end solves) neither map nor unmap memory nor synchronise the device.
+cudaMemPool_t ttc_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  uint64_t keep = ~0ull;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  pools[dev] = pool;
+  return pool;
+}
+
+cudaError_t ttc_pool_alloc(void** p, size_t bytes, cudaStream_t st) {
+  cudaMemPool_t pool = ttc_pool();
+  if (!pool) return cudaMalloc(p, bytes);
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+void ttc_pool_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
 int ttc_alloc(ttc_ctx* c, void** p, size_t bytes, bool obs) {
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  cudaError_t e = ttc_pool_alloc(&q, bytes ? bytes : 16, c->stream);
   if (e != cudaSuccess) {
     ttc_record_cuda_error(e);
     cudaGetLastError();
@@ -55,7 +96,7 @@ int ttc_alloc(ttc_ctx* c, void** p, size_t bytes, bool obs) {
 
 void ttc_free_obs(ttc_ctx* c) {
   for (auto& b : c->obs_bufs) {
-    cudaFree(b.p);
+    ttc_pool_free(b.p, c->stream);
     c->device_bytes -= b.bytes;
   }
   c->obs_bufs.clear();
@@ -271,8 +312,8 @@ int ttc_create(ttc_ctx** out, int d, const int64_t* n, const int32_t* r, const t
     size_t padcnt = (size_t)n[k] * c->rank_bucket * c->rank_bucket;
     if ((s = ttc_alloc(c, (void**)&P.core32p[k], sizeof(float) * padcnt, false)) != TTC_OK) break;
     if ((s = ttc_alloc(c, (void**)&P.core64p[k], sizeof(double) * padcnt, false)) != TTC_OK) break;
-    cudaMemset(P.core32p[k], 0, sizeof(float) * padcnt);
-    cudaMemset(P.core64p[k], 0, sizeof(double) * padcnt);
+    cudaMemsetAsync(P.core32p[k], 0, sizeof(float) * padcnt, c->stream);
+    cudaMemsetAsync(P.core64p[k], 0, sizeof(double) * padcnt, c->stream);
     if ((s = ttc_alloc(c, (void**)&P.s[k], sizeof(double) * (size_t)n[k], false)) != TTC_OK) break;
     if ((s = ttc_alloc(c, (void**)&P.E[k], sizeof(double) * cnt, false)) != TTC_OK) break;
   }
@@ -281,7 +322,8 @@ int ttc_create(ttc_ctx** out, int d, const int64_t* n, const int32_t* r, const t
   if (s == TTC_OK) s = ttc_alloc_dense(c);
   if (s == TTC_OK) {
     double v[2] = {c->opt.eps_rel, c->opt.alpha_scale};
-    cudaError_t e = cudaMemcpy(P.scal + SC_EPS_REL, v, sizeof(v), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpyAsync(P.scal + SC_EPS_REL, v, sizeof(v), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // allocations ready for every stream
     if (e != cudaSuccess) {
       ttc_record_cuda_error(e);
       s = TTC_ECUDA;
@@ -304,8 +346,9 @@ void ttc_destroy(ttc_ctx* c) {
   if (c->ev_end) cudaEventDestroy(c->ev_end);
   ttc_fork_destroy(c->fork);
   ttc_free_obs(c);
-  for (auto& b : c->bufs) cudaFree(b.p);
+  for (auto& b : c->bufs) ttc_pool_free(b.p, c->stream);
   c->bufs.clear();
+  cudaStreamSynchronize(c->stream);
   ttc_free_plan(c);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -566,11 +609,11 @@ int ttc_eval(ttc_ctx* c, int64_t M, const int32_t* idx, int precision, double* o
     }
   int32_t* di = nullptr;
   double* dout = nullptr;
-  cudaError_t e1 = cudaMalloc(&di, sizeof(int32_t) * (size_t)M * c->m);
-  cudaError_t e2 = cudaMalloc(&dout, sizeof(double) * (size_t)M);
+  cudaError_t e1 = ttc_pool_alloc((void**)&di, sizeof(int32_t) * (size_t)M * c->m, c->stream);
+  cudaError_t e2 = ttc_pool_alloc((void**)&dout, sizeof(double) * (size_t)M, c->stream);
   if (e1 != cudaSuccess || e2 != cudaSuccess) {
-    cudaFree(di);
-    cudaFree(dout);
+    ttc_pool_free(di, c->stream);
+    ttc_pool_free(dout, c->stream);
     ttc_record_cuda_error(e1 != cudaSuccess ? e1 : e2);
     return TTC_ENOMEM;
   }
@@ -580,8 +623,8 @@ int ttc_eval(ttc_ctx* c, int64_t M, const int32_t* idx, int precision, double* o
   if (e == cudaSuccess && s == TTC_OK)
     e = cudaMemcpyAsync(out, dout, sizeof(double) * (size_t)M, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  cudaFree(di);
-  cudaFree(dout);
+  ttc_pool_free(di, c->stream);
+  ttc_pool_free(dout, c->stream);
   if (e != cudaSuccess) {
     ttc_record_cuda_error(e);
     return TTC_ECUDA;

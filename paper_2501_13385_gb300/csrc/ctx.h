@@ -79,6 +79,9 @@ void ttc_solve_after(ttc_ctx* c, SolveState& st, const double* sc, bool checked)
 bool ttc_solve_needs_metric(const ttc_ctx* c, int it);
 int ttc_read_scalars(ttc_ctx* c, double* out);
 
+// allocation helpers (api.cu): the library's stream-ordered device pool
+cudaError_t ttc_pool_alloc(void** p, size_t bytes, cudaStream_t st);
+void ttc_pool_free(void* p, cudaStream_t st);
 // allocation helpers (api.cu)
 int ttc_alloc(ttc_ctx* c, void** p, size_t bytes, bool obs);
 void ttc_free_obs(ttc_ctx* c);

@@ -1159,13 +1159,15 @@ int ttc_alloc_dense(ttc_ctx* c) {
   }
   double* small = nullptr;
   TTC_TRY(ttc_alloc(c, (void**)&small, sizeof(double) * (size_t)off, false));
-  TTC_CUDA(cudaMemset(small, 0, sizeof(double) * (size_t)off));
+  TTC_CUDA(cudaMemsetAsync(small, 0, sizeof(double) * (size_t)off, c->stream));
   P.small = small;
   double one = 1.0;
-  TTC_CUDA(cudaMemcpy(small + P.off_lam[0], &one, sizeof(double), cudaMemcpyHostToDevice));
-  TTC_CUDA(cudaMemcpy(small + P.off_gam[m], &one, sizeof(double), cudaMemcpyHostToDevice));
-  TTC_CUDA(cudaMemcpy(small + P.off_psi[m], &one, sizeof(double), cudaMemcpyHostToDevice));
-  for (int t = 0; t < 3; ++t) TTC_CUDA(cudaMemcpy(small + P.off_mlam[t][0], &one, sizeof(double), cudaMemcpyHostToDevice));
+  TTC_CUDA(cudaMemcpyAsync(small + P.off_lam[0], &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  TTC_CUDA(cudaMemcpyAsync(small + P.off_gam[m], &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  TTC_CUDA(cudaMemcpyAsync(small + P.off_psi[m], &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  for (int t = 0; t < 3; ++t)
+    TTC_CUDA(cudaMemcpyAsync(small + P.off_mlam[t][0], &one, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  TTC_CUDA(cudaStreamSynchronize(c->stream));   // `one` lives on this stack frame
   for (int k = 0; k < m; ++k) {
     double* Ck = nullptr;
     TTC_TRY(ttc_alloc(c, (void**)&Ck, sizeof(double) * (size_t)c->n[k] * P.q[k] * P.q[k + 1], false));
@@ -1187,12 +1189,12 @@ int ttc_alloc_dense(ttc_ctx* c) {
   }
   double* scal = nullptr;
   TTC_TRY(ttc_alloc(c, (void**)&scal, sizeof(double) * SC_COUNT, false));
-  TTC_CUDA(cudaMemset(scal, 0, sizeof(double) * SC_COUNT));
+  TTC_CUDA(cudaMemsetAsync(scal, 0, sizeof(double) * SC_COUNT, c->stream));
   P.scal = scal;
   P.flags = reinterpret_cast<unsigned*>(scal + SC_FLAGS);
   int* counters = nullptr;
   TTC_TRY(ttc_alloc(c, (void**)&counters, sizeof(int) * 128, false));
-  TTC_CUDA(cudaMemset(counters, 0, sizeof(int) * 128));
+  TTC_CUDA(cudaMemsetAsync(counters, 0, sizeof(int) * 128, c->stream));
   P.counters = counters;
 
   Plan pl;

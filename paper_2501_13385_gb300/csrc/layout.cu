@@ -227,8 +227,9 @@ int ttc_build_layout(ttc_ctx* c, const int32_t* idx_host, const double* y_host) 
   long long maxn = 0;
   for (int k = 0; k < m; ++k) maxn = std::max(maxn, c->n[k]);
   auto cleanup = [&]() {
-    cudaFree(idx_d); cudaFree(y_d); cudaFree(code_in); cudaFree(pa); cudaFree(pb); cudaFree(pt);
-    cudaFree(counts); cudaFree(flags); cudaFree(scr);
+    for (void* q : {(void*)idx_d, (void*)y_d, (void*)code_in, (void*)pa, (void*)pb, (void*)pt, (void*)counts,
+                    (void*)flags, (void*)scr})
+      ttc_pool_free(q, st);
   };
 #define LTRY(call)                        \
   do {                                    \
@@ -239,15 +240,15 @@ int ttc_build_layout(ttc_ctx* c, const int32_t* idx_host, const double* y_host) 
       return _e == cudaErrorMemoryAllocation ? TTC_ENOMEM : TTC_ECUDA; \
     }                                     \
   } while (0)
-  LTRY(cudaMalloc(&idx_d, sizeof(int32_t) * (size_t)N * m));
-  LTRY(cudaMalloc(&y_d, sizeof(double) * (size_t)N));
-  LTRY(cudaMalloc(&code_in, sizeof(uint32_t) * (size_t)N * W));
-  LTRY(cudaMalloc(&pa, sizeof(int) * (size_t)N));
-  LTRY(cudaMalloc(&pb, sizeof(int) * (size_t)N));
-  LTRY(cudaMalloc(&pt, sizeof(int) * (size_t)N));
-  LTRY(cudaMalloc(&counts, sizeof(int) * (size_t)std::max(ncount_max, maxn + 2)));
-  LTRY(cudaMalloc(&flags, sizeof(int) * 4));
-  LTRY(cudaMalloc(&scr, sizeof(int) * (size_t)(maxn + 2)));
+  LTRY(ttc_pool_alloc((void**)&idx_d, sizeof(int32_t) * (size_t)N * m, st));
+  LTRY(ttc_pool_alloc((void**)&y_d, sizeof(double) * (size_t)N, st));
+  LTRY(ttc_pool_alloc((void**)&code_in, sizeof(uint32_t) * (size_t)N * W, st));
+  LTRY(ttc_pool_alloc((void**)&pa, sizeof(int) * (size_t)N, st));
+  LTRY(ttc_pool_alloc((void**)&pb, sizeof(int) * (size_t)N, st));
+  LTRY(ttc_pool_alloc((void**)&pt, sizeof(int) * (size_t)N, st));
+  LTRY(ttc_pool_alloc((void**)&counts, sizeof(int) * (size_t)std::max(ncount_max, maxn + 2), st));
+  LTRY(ttc_pool_alloc((void**)&flags, sizeof(int) * 4, st));
+  LTRY(ttc_pool_alloc((void**)&scr, sizeof(int) * (size_t)(maxn + 2), st));
   LTRY(cudaMemcpyAsync(idx_d, idx_host, sizeof(int32_t) * (size_t)N * m, cudaMemcpyHostToDevice, st));
   LTRY(cudaMemcpyAsync(y_d, y_host, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, st));
   LTRY(cudaMemsetAsync(flags, 0, sizeof(int) * 4, st));

@@ -559,7 +559,20 @@ __global__ void __launch_bounds__(kThreads) k_stage(const DevProb P, const Stage
 // warp order, so results stay reproducible.
 
 constexpr int kWarpsW = kThreads / 32;
-constexpr int kWScr = 3 * 16 * 16;   // doubles of scratch per warp
+constexpr int kWScr = 3 * 16 * 16;   // doubles of scratch per warp at most (q = 16)
+
+// a warp's scratch: three q_max x q_max matrices of the problem (so blocks of
+// small problems take little shared memory and more of them stay resident)
+__device__ __forceinline__ int wscr_mat(const DevProb& P) {
+  int q = 1;
+  for (int k = 0; k <= P.m; ++k) q = max(q, P.q[k]);
+  return q * q;
+}
+inline int wscr_mat_host(const DevProb& P) {
+  int q = 1;
+  for (int k = 0; k <= P.m; ++k) q = std::max(q, P.q[k]);
+  return q * q;
+}
 
 // Y (M x N, ld N) = X (M x K, ld ldx) Z (K x N, ld ldz), spread over the lanes
 __device__ __forceinline__ void warp_mm(double* Y, const double* X, int ldx, const double* Z, int ldz, int M, int N,
@@ -617,7 +630,7 @@ __device__ void warp_contrib(const DevProb& P, const Job& J, int x, double (&acc
   const int k = J.k;
   const int ra = P.r[k], rb = P.r[k + 1];
   double* A = scr;
-  double* Y = scr + 256;
+  double* Y = scr + wscr_mat(P);
   switch (J.op) {
     case OP_LAM: {   // acc += w2 T^T (Lam T)
       warp_load(A, P.core64[k] + (long long)x * ra * rb, ra * rb);
@@ -666,8 +679,8 @@ __device__ void warp_slice_map(const DevProb& P, int k, int x, double* scr) {
   const int qa = P.q[k], qb = P.q[k + 1];
   const int ra = P.r[k], rb = P.r[k + 1];
   double* A = scr;
-  double* Y = scr + 256;
-  double* Z = scr + 512;
+  double* Y = scr + wscr_mat(P);
+  double* Z = scr + 2 * wscr_mat(P);
   warp_load(A, P.C[k] + (long long)x * qa * qb, qa * qb);
   const double* Cp = A;
   if (k > 0) {
@@ -698,7 +711,7 @@ __global__ void __launch_bounds__(kThreads) k_stage_w(const DevProb P, const Sta
   extern __shared__ __align__(16) double sm[];
   __shared__ int am_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* scr = sm + warp * kWScr;
+  double* scr = sm + warp * 3 * wscr_mat(P);
   int b = blockIdx.x;
   for (int i = 0; i < S.nmap; ++i) {     // slice maps first, one slice per warp
     const int k = S.map_k[i];
@@ -768,7 +781,7 @@ __global__ void __launch_bounds__(kThreads) k_stage_w(const DevProb P, const Sta
 __global__ void __launch_bounds__(kThreads) k_build_C_w(const DevProb P, int nslices) {
   extern __shared__ __align__(16) double sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* scr = sm + warp * kWScr;
+  double* scr = sm + warp * 3 * wscr_mat(P);
   int g = blockIdx.x * kWarpsW + warp;
   if (g >= nslices) return;
   int k = 0;
@@ -781,8 +794,8 @@ __global__ void __launch_bounds__(kThreads) k_build_C_w(const DevProb P, int nsl
   const double alpha = P.scal[SC_ALPHA];
   const double wi = gpow(P, k, x, -1);
   double* Tt = scr;
-  double* t1 = scr + 256;
-  double* B = scr + 512;
+  double* t1 = scr + wscr_mat(P);
+  double* B = scr + 2 * wscr_mat(P);
   warp_load(Tt, P.core64[k] + (long long)x * ra * rb, ra * rb);
   warp_mm(t1, P.small + P.off_lami[k], ra, P.E[k] + (long long)x * ra * rb, rb, ra, rb, ra, 1.0);
   warp_mm(B, t1, rb, P.small + P.off_gami[k + 1], rb, ra, rb, rb, -alpha * wi);
@@ -1289,7 +1302,8 @@ int ttc_alloc_dense(ttc_ctx* c) {
   size_t bond_need = sizeof(double) * (size_t)(2 * qmax * qmax + 5 * qmax * rmax + 6 * rmax * rmax + kThreads) +
                      sizeof(float) * (size_t)(2 * rmax * rmax);
   pl.smem_stage = std::max(red_need, std::max(proj_need, bond_need)) + 64;
-  pl.smem_warp = std::max(pl.smem_stage, sizeof(double) * (size_t)kWarpsW * kWScr);
+  pl.smem_warp = pl.warp ? std::max(pl.smem_stage, sizeof(double) * (size_t)kWarpsW * 3 * wscr_mat_host(P))
+                         : pl.smem_stage;
   {
     // the attribute is per device and shared by every context: only raise it,
     // so that contexts needing more than this one keep launching
@@ -1335,7 +1349,8 @@ int ttc_launch_dense(ttc_ctx* c) {
     c->nlaunch += 2;
   }
   if (pl.warp)
-    k_build_C_w<<<(nslices + kWarpsW - 1) / kWarpsW, kThreads, sizeof(double) * kWarpsW * kWScr, st>>>(P, nslices);
+    k_build_C_w<<<(nslices + kWarpsW - 1) / kWarpsW, kThreads, sizeof(double) * kWarpsW * 3 * wscr_mat_host(P), st>>>(
+        P, nslices);
   else
     k_build_C<<<nslices, 128, 0, st>>>(P);
   TTC_CUDA(cudaGetLastError());

@@ -72,7 +72,7 @@ struct Stage {
 };
 
 constexpr int kThreads = 256;
-constexpr int kMaxIter = 64;          // subspace iterations per bond
+constexpr int kMaxIter = 32;          // subspace iterations per bond (then the exact eigensolver)
 constexpr double kMoveTol2 = 1e-28;   // squared subspace movement per basis vector at convergence
 
 // y = v^{-1/(2m)} by Newton's iteration for inverse roots,
@@ -308,6 +308,7 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
   float* Lf = reinterpret_cast<float*>(red + blockDim.x);
   float* Lif = Lf + r * r;
   __shared__ int bad;
+  __shared__ double scl[2];   // powers of two that scale Psi and N to unit size
   for (int i = tid; i < q * q; i += blockDim.x) N[i] = P.small[P.off_nk[k] + i];
   if (tid == 0) bad = 0;
   __syncthreads();
@@ -315,22 +316,32 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
     // A = Psi N from operands scaled by powers of two to unit size: its
     // invariant subspaces do not depend on the scale, and Psi N itself grows
     // with the fourth power of the iterate's entries
+    // (both are SPD Grams: the largest entry is on the diagonal)
     const double* Psi = P.small + P.off_psi[k + 1];
-    double mp = 0.0, mn = 0.0;
-    for (int i = tid; i < q * q; i += blockDim.x) {
-      mp = nanmax(mp, fabs(Psi[i]));
-      mn = nanmax(mn, fabs(N[i]));
+    if (tid < 32) {
+      double mp = 0.0, mn = 0.0;
+      for (int i = tid; i < q; i += 32) {
+        mp = nanmax(mp, fabs(Psi[i * q + i]));
+        mn = nanmax(mn, fabs(N[i * q + i]));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        mp = nanmax(mp, __shfl_xor_sync(0xffffffffu, mp, o));
+        mn = nanmax(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      }
+      if (tid == 0) {
+        int ep = 0, en = 0;
+        if (mp > 0.0 && mp <= 1.7e308) frexp(mp, &ep);
+        if (mn > 0.0 && mn <= 1.7e308) frexp(mn, &en);
+        scl[0] = ldexp(1.0, -ep);
+        scl[1] = ldexp(1.0, -en);
+      }
     }
-    mp = blk_max(mp, red);
-    mn = blk_max(mn, red);
-    int ep = 0, en = 0;
-    if (mp > 0.0 && mp <= 1.7e308) frexp(mp, &ep);
-    if (mn > 0.0 && mn <= 1.7e308) frexp(mn, &en);
+    __syncthreads();
     double* Ps = scr;   // q*q <= 2 q r
     double* Ns = W;     // W and V: 2 q r >= q*q doubles
     for (int i = tid; i < q * q; i += blockDim.x) {
-      Ps[i] = ldexp(Psi[i], -ep);
-      Ns[i] = ldexp(N[i], -en);
+      Ps[i] = Psi[i] * scl[0];
+      Ns[i] = N[i] * scl[1];
     }
     __syncthreads();
     blk_gemm<double>(q, q, q, Ps, q, false, Ns, q, false, A, q, 1.0, false);
@@ -362,6 +373,47 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
       ++it;
       break;
     }
+  }
+  if (it == kMaxIter) {
+    // The subspace did not settle (a near tie of the r-th and (r+1)-th
+    // singular values at this bond): take it exactly from symmetric
+    // eigendecompositions of the scaled operators, Psi = Q diag(d) Q^T,
+    // S = Psi^{1/2}, M = S N S = V diag(w) V^T; then Psi N (S V) = (S V) diag(w),
+    // so the top r columns of S V span the invariant subspace.
+    const double* Psi = P.small + P.off_psi[k + 1];
+    double* X1 = A;                 // N stays; the regions after it are free now
+    double* Q = X1 + q * q;
+    double* dv = Q + q * q;
+    double* T1 = dv + q;
+    double* wk = T1 + q * q;        // q*q + 448 doubles for the Jacobi solver
+    for (int i = tid; i < q * q; i += blockDim.x) X1[i] = Psi[i] * scl[0];
+    __syncthreads();
+    blk_sym_eig(X1, q, Q, dv, wk);
+    for (int i = tid; i < q * q; i += blockDim.x) {                                // S = Q diag(sqrt d) Q^T
+      const int a = i / q, b = i - (i / q) * q;
+      double acc = 0.0;
+      for (int t = 0; t < q; ++t) acc = fma(Q[a * q + t] * sqrt(fmax(dv[t], 0.0)), Q[b * q + t], acc);
+      X1[i] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < q * q; i += blockDim.x) {                                // T1 = (N scaled) S
+      const int a = i / q, b = i - (i / q) * q;
+      double acc = 0.0;
+      for (int t = 0; t < q; ++t) acc = fma(N[a * q + t] * scl[1], X1[t * q + b], acc);
+      T1[i] = acc;
+    }
+    __syncthreads();
+    blk_gemm<double>(q, q, q, X1, q, false, T1, q, false, Q, q, 1.0, false);      // M = S T1
+    __syncthreads();
+    blk_sym_eig(Q, q, T1, dv, wk);                                                 // V (descending) into T1
+    for (int i = tid; i < q * r; i += blockDim.x) {                                // W = S V[:, :r]
+      const int a = i / r, c = i - (i / r) * r;
+      double acc = 0.0;
+      for (int t = 0; t < q; ++t) acc = fma(X1[a * q + t], T1[t * q + c], acc);
+      W[i] = acc;
+    }
+    __syncthreads();
+    orthonormalize(W, q, r, U, scr, red, Lf, Lif, &bad);
   }
   // normalisation: T_k = C' U R^{-1} with R^T R = G = U^T N U; R^{-1} from the
   // FP32 Cholesky of G checked by E = R^{-T} G R^{-1} - I (FP64 Cholesky when
@@ -1301,6 +1353,8 @@ int ttc_alloc_dense(ttc_ctx* c) {
   size_t proj_need = sizeof(double) * (size_t)(8 * 2 * rmax * rmax) + sizeof(float) * (size_t)(8 * 2 * rmax * rmax);
   size_t bond_need = sizeof(double) * (size_t)(2 * qmax * qmax + 5 * qmax * rmax + 6 * rmax * rmax + kThreads) +
                      sizeof(float) * (size_t)(2 * rmax * rmax);
+  // the bond's exact fallback: N, then 4 q^2 + q doubles plus the Jacobi solver's 448
+  bond_need = std::max(bond_need, sizeof(double) * (size_t)(5 * qmax * qmax + qmax + 448 + kThreads));
   pl.smem_stage = std::max(red_need, std::max(proj_need, bond_need)) + 64;
   pl.smem_warp = pl.warp ? std::max(pl.smem_stage, sizeof(double) * (size_t)kWarpsW * 3 * wscr_mat_host(P))
                          : pl.smem_stage;

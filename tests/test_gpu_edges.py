@@ -1,0 +1,66 @@
+"""Edge cases of the CUDA path against the oracle: a single observation, the
+largest order (16), a mode of size 1 (a zero-bit code field), the largest
+rank (32), two-word packed codes, all ranks 1, and empty or oversized inputs
+rejected.  FP64 steps within 1e-10 of the oracle.  GPU only."""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_2501_13385_gb300 import ttc
+from paper_2501_13385_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2501_13385_gb300 import build
+    build.build()
+    ttc.lib()
+
+
+def fp64_step_matches(P, steps=1, tol=1e-10):
+    cur = P.init
+    with ttc.Context(P.n, P.r, precision=ttc.PREC_FP64) as c:
+        c.set_observations(P.idx, P.y)
+        c.set_cores(P.init)
+        for _ in range(steps):
+            info = c.step()
+            cur, oi = o.prgd_step(cur, P.idx, P.y, P.n, P.r, eps_rel=1.0, alpha_scale=1.5)
+            assert info["alpha"] == pytest.approx(oi.alpha, rel=1e-12)
+            assert o.tt_dist(c.get_cores(), cur) <= tol * o.tt_norm(cur)
+        # the sampled values agree too (FP64 evaluation at Omega)
+        v = c.eval(P.idx, ttc.PREC_FP64)
+        assert np.max(np.abs(v - o.tt_eval(cur, P.idx))) <= 1e-12 * max(1.0, np.max(np.abs(v)))
+
+
+@pytest.mark.parametrize("case", [
+    ("single_entry", dict(n=[3, 4, 5], r=[1, 1, 1, 1], count=1)),
+    ("all_ranks_one", dict(n=[20, 30, 25], r=[1, 1, 1, 1], count=400)),
+    ("order_16", dict(n=[2] * 16, r=[1, 2, 3] + [4] * 11 + [3, 2, 1], count=6000)),
+    ("mode_of_size_one", dict(n=[9, 1, 8, 7], r=[1, 3, 3, 3, 1], count=300)),
+    ("two_word_codes", dict(n=[5000, 4000, 3000], r=[1, 3, 3, 1], count=20000)),
+    ("rank_32", dict(n=[64, 64, 64], r=[1, 32, 32, 1], count=100000)),
+    ("order_2_matrix", dict(n=[120, 90], r=[1, 6, 1], count=4000)),
+], ids=lambda c: c[0])
+def test_edge_shapes_fp64_step(case):
+    _, spec = case
+    P = w.random_problem(77, spec["n"], spec["r"], spec["count"], init_rel=0.1)
+    fp64_step_matches(P, steps=2 if spec["count"] > 1 else 1)
+
+
+def test_empty_and_oversized_inputs_are_rejected():
+    with ttc.Context([5, 6, 7], [1, 2, 2, 1]) as c:
+        with pytest.raises(ttc.TTCError) as e:
+            c.set_observations(np.zeros((0, 3), dtype=np.int32), np.zeros(0))
+        assert e.value.status == -1
+    with pytest.raises(ttc.TTCError) as e:                 # order above 16
+        ttc.Context([2] * 17, [1] + [2] * 16 + [1])
+    assert e.value.status == -10
+    with pytest.raises(ttc.TTCError) as e:                 # rank above 32
+        ttc.Context([64, 64, 64], [1, 33, 33, 1])
+    assert e.value.status == -10
+    with pytest.raises(ttc.TTCError) as e:                 # codes wider than 128 bits
+        ttc.Context([1 << 17] * 7, [1] + [2] * 6 + [1]).set_observations(
+            np.zeros((1, 7), dtype=np.int32), np.zeros(1))
+    assert e.value.status in (-10, -1)

@@ -253,11 +253,12 @@ __device__ void orthonormalize(const double* W, int q, int r, double* U, double*
     if (tid < 32) warp_chol_inv32(G, r, r, Lf, Lif, &pow2[0]);
     __syncthreads();
     double* dst = (pass == 0) ? Z : Z2;
+    const double sc = ldexp(1.0, -pow2[0]);   // exact power of two
     for (int i = tid; i < q * r; i += blockDim.x) {                               // dst = src L^{-T}
       int a = i / r, c = i - (i / r) * r;
       double acc = 0.0;
       for (int t = 0; t <= c; ++t) acc = fma(src[a * r + t], (double)Lif[c * r + t], acc);
-      dst[i] = ldexp(acc, -pow2[0]);
+      dst[i] = acc * sc;
     }
     __syncthreads();
     blk_gemm<double>(r, r, q, dst, r, true, dst, r, false, E, r, 1.0, false);   // E = dst^T dst - I
@@ -431,9 +432,10 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
   if (tid < 32) warp_chol_inv32(G, r, r, Lf, Lif, &pow2n[0]);
   __syncthreads();
   double* Rinv = Bm;
+  const double scn = ldexp(1.0, -pow2n[0]);
   for (int i = tid; i < r * r; i += blockDim.x) {                                 // Rinv = L^{-T}
     int a = i / r, c = i - (i / r) * r;
-    Rinv[i] = ldexp((double)Lif[c * r + a], -pow2n[0]);
+    Rinv[i] = (double)Lif[c * r + a] * scn;
   }
   __syncthreads();
   for (int attempt = 0; attempt < 2; ++attempt) {

@@ -203,9 +203,10 @@ static __device__ int warp_chol_inv32(const double* A, int lda, int n, float* L,
     }
     *pow2 = k2;
   }
+  const double sc = ldexp(1.0, -2 * k2);   // exact power of two
   for (int idx = lane; idx < n * n; idx += 32) {
     int i = idx / n, k = idx - (idx / n) * n;
-    L[idx] = (k <= i) ? (float)ldexp(A[i * lda + k], -2 * k2) : 0.f;
+    L[idx] = (k <= i) ? (float)(A[i * lda + k] * sc) : 0.f;
   }
   __syncwarp();
   float scale = 0.f;
@@ -268,12 +269,13 @@ static __device__ double warp_spd_inverse(const double* A, int lda, int n, doubl
   const int lane = threadIdx.x & 31;
   int k2 = 0;
   int bad = warp_chol_inv32(A, lda, n, L, Li, &k2);
+  const double sc = ldexp(1.0, -2 * k2);
   for (int idx = lane; idx < n * n; idx += 32) {
     int i = idx / n, j = idx - (idx / n) * n;
     int k0 = i > j ? i : j;
     double acc = 0.0;
     for (int k = k0; k < n; ++k) acc = fma((double)Li[k * n + i], (double)Li[k * n + j], acc);
-    X[i * ldx + j] = ldexp(acc, -2 * k2);   // A^{-1} = 2^{-2k} (A 2^{-2k})^{-1}
+    X[i * ldx + j] = acc * sc;   // A^{-1} = 2^{-2k} (A 2^{-2k})^{-1}
   }
   __syncwarp();
   double* T1 = T;

@@ -121,8 +121,8 @@ int drop_graphs(ttc_ctx* c) {
 
 // the fixed launch sequence of one iteration
 int enqueue_iteration(ttc_ctx* c, int prec) {
-  TTC_TRY(ttc_launch_save_prev(c));
   TTC_TRY(ttc_launch_omega_pass(c, prec));
+  TTC_TRY(ttc_launch_save_prev(c));   // also the slice weights, which need this step's eps
   TTC_TRY(ttc_launch_dense(c));
   return TTC_OK;
 }
@@ -315,6 +315,7 @@ int ttc_create(ttc_ctx** out, int d, const int64_t* n, const int32_t* r, const t
     cudaMemsetAsync(P.core32p[k], 0, sizeof(float) * padcnt, c->stream);
     cudaMemsetAsync(P.core64p[k], 0, sizeof(double) * padcnt, c->stream);
     if ((s = ttc_alloc(c, (void**)&P.s[k], sizeof(double) * (size_t)n[k], false)) != TTC_OK) break;
+    if ((s = ttc_alloc(c, (void**)&P.wt[k], sizeof(double) * 2 * (size_t)n[k], false)) != TTC_OK) break;
     if ((s = ttc_alloc(c, (void**)&P.E[k], sizeof(double) * cnt, false)) != TTC_OK) break;
   }
   if (s == TTC_OK) s = ttc_fork_create(c->fork);

@@ -31,6 +31,8 @@ struct ttc_batch {
     std::vector<int> idx;
   };
   std::vector<Group> groups;
+  std::vector<DenseGroup*> dense;   // batched dense stages (members grouped by order)
+  std::vector<int> in_dense;        // per member: its dense group, or -1 (own graph branch)
   cudaGraphExec_t exec = nullptr;
   long long kernels_per_step = 0;
   long long nlaunch = 0;
@@ -43,6 +45,9 @@ struct ttc_batch {
 namespace {
 
 void free_groups(ttc_batch* b) {
+  for (auto* d : b->dense) ttc_dense_group_destroy(d);
+  b->dense.clear();
+  b->in_dense.clear();
   for (auto& G : b->groups) {
     cudaFree(G.probs);
     cudaFree(G.pass_base);
@@ -114,6 +119,28 @@ int build_groups(ttc_batch* b) {
     G.g.tab_rows = tb.back();
     b->groups.push_back(G);
   }
+  // members whose dense stages can be batched, grouped by order
+  b->in_dense.assign(b->members.size(), -1);
+  std::vector<int> orders;
+  for (auto* c : b->members)
+    if (ttc_dense_batchable(c) && std::find(orders.begin(), orders.end(), c->m) == orders.end()) orders.push_back(c->m);
+  for (int m : orders) {
+    std::vector<ttc_ctx*> mem;
+    std::vector<int> at;
+    for (int i = 0; i < (int)b->members.size(); ++i)
+      if (b->members[i]->m == m && ttc_dense_batchable(b->members[i])) {
+        mem.push_back(b->members[i]);
+        at.push_back(i);
+      }
+    DenseGroup* d = nullptr;
+    int s = ttc_dense_group_create(mem.data(), (int)mem.size(), &d);
+    if (s != TTC_OK) {
+      free_groups(b);
+      return s;
+    }
+    for (int i : at) b->in_dense[i] = (int)b->dense.size();
+    b->dense.push_back(d);
+  }
   return TTC_OK;
 }
 
@@ -153,7 +180,11 @@ int capture(ttc_batch* b) {
       ++batched;
     }
   if (s == TTC_OK && e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
+  long long dense_kernels = 0;
+  for (auto* d : b->dense)
+    if (s == TTC_OK && e == cudaSuccess) s = ttc_dense_group_launch(d, b->stream, &dense_kernels);
   for (size_t i = 0; i < b->members.size() && s == TTC_OK && e == cudaSuccess; ++i) {
+    if (b->in_dense[i] >= 0) continue;   // its dense stages ran batched above
     ttc_ctx* c = b->members[i];
     bool own = c->stream != b->stream;
     for (size_t j = 0; j < i && own; ++j)
@@ -170,7 +201,7 @@ int capture(ttc_batch* b) {
     c->stream = saved;
   }
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
-  long long kernels = batched;
+  long long kernels = batched + dense_kernels;
   for (size_t i = 0; i < b->members.size(); ++i) {
     kernels += b->members[i]->nlaunch - before[i];
     b->members[i]->nlaunch = before[i];

@@ -81,6 +81,7 @@ struct DevProb {
 
   // outputs of the Omega pass
   double* s[TTC_MAXM];           // slice energies, n_k
+  double* wt[TTC_MAXM];          // this step's slice weights, n_k x 2: G_k(x)^{+1/(2m)}, G_k(x)^{-1/(2m)}
   double* E[TTC_MAXM];           // n_k x r_k x r_{k+1}
   double* B1[TTC_MAXM];          // steepest step: update cores at unit step, n_k x r_k x r_{k+1}
   double* zw;                    // steepest step: per slice G^{1/(2m)} <Lam B1 Gam, B1> (all modes)

@@ -169,6 +169,13 @@ int ttc_launch_omega_pass(ttc_ctx* c, int prec);
 int ttc_launch_eval(ttc_ctx* c, const int32_t* idx_dev, long long M, int prec, double* out_dev);
 
 // dense.cu
+// batched dense stages: members on the warp path without the steepest step
+// and of one order run each dense stage as one launch
+struct DenseGroup;
+bool ttc_dense_batchable(const ttc_ctx* c);
+int ttc_dense_group_create(ttc_ctx* const* members, int count, DenseGroup** out);
+int ttc_dense_group_launch(const DenseGroup* g, cudaStream_t st, long long* kernels);
+void ttc_dense_group_destroy(DenseGroup* g);
 int ttc_alloc_dense(ttc_ctx* c);
 int ttc_launch_dense(ttc_ctx* c);
 int ttc_launch_metric(ttc_ctx* c, int which);   // 0: ||T - T*||^2 , 1: ||T_l - T_{l-1}||^2

@@ -42,6 +42,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <new>
 #include <mutex>
 #include <vector>
 
@@ -100,13 +101,27 @@ __device__ __forceinline__ double inv_root(double v, int m) {
   for (int it = 0; it < 2; ++it) y = y * fma(c, fma(-v, ipow_2m(y, two_m), 1.0), 1.0);
   return y;
 }
+// the slice weights of this step, G_k(x) = eps + s_k(x) (Eq. 3.2's diagonal
+// preconditioner): wt[k][2x] = G^{+1/(2m)}, wt[k][2x+1] = G^{-1/(2m)}, one
+// thread per slice, written once per step after the slice energies and eps
+// are final and read by every dense stage
+__device__ __forceinline__ void slice_weights(const DevProb& P, long long t, long long nt) {
+  if (P.uniform) return;
+  const double eps = P.scal[SC_EPS];
+  for (int k = 0; k < P.m; ++k) {
+    for (long long x = t; x < P.n[k]; x += nt) {
+      const double v = eps + P.s[k][x];
+      const double y = inv_root(v, P.m);                                  // v^{-1/(2m)}
+      P.wt[k][2 * x] = v * ipow_2m(y, 2 * P.m - 1);                       // v^{1/(2m)} = v * y^{2m-1}
+      P.wt[k][2 * x + 1] = y;
+    }
+  }
+}
 // G_k(x)^{+1/(2m)} (sign > 0) or G_k(x)^{-1/(2m)} (sign < 0); 1 with the
 // uniform metric (RGD)
 __device__ __forceinline__ double gpow(const DevProb& P, int k, int x, int sign) {
   if (P.uniform) return 1.0;
-  const double v = P.scal[SC_EPS] + P.s[k][x];
-  const double y = inv_root(v, P.m);            // v^{-1/(2m)}
-  return sign < 0 ? y : v * ipow_2m(y, 2 * P.m - 1);   // v^{1/(2m)} = v * y^{2m-1}
+  return P.wt[k][2 * x + (sign < 0 ? 1 : 0)];
 }
 
 // ---- per-slice contributions ------------------------------------------------
@@ -628,17 +643,28 @@ inline int wscr_mat_host(const DevProb& P) {
   return q * q;
 }
 
-// Y (M x N, ld N) = X (M x K, ld ldx) Z (K x N, ld ldz), spread over the lanes
-__device__ __forceinline__ void warp_mm(double* Y, const double* X, int ldx, const double* Z, int ldz, int M, int N,
-                                        int K, double alpha) {
+// Y (M x N, ld N) = alpha X (M x K, ld ldx) Z (K x N, ld ldz), spread over
+// the lanes; the unscaled form spends no FP64 multiply on alpha = 1 (the FP64
+// pipe is the bound of the batched dense stages on this GPU)
+template <bool kScale>
+__device__ __forceinline__ void warp_mm_t(double* Y, const double* X, int ldx, const double* Z, int ldz, int M, int N,
+                                          int K, double alpha) {
   const int lane = threadIdx.x & 31;
   for (int e = lane; e < M * N; e += 32) {
     const int i = e / N, j = e - (e / N) * N;
     double acc = 0.0;
     for (int t = 0; t < K; ++t) acc = fma(X[i * ldx + t], Z[t * ldz + j], acc);
-    Y[e] = alpha * acc;
+    Y[e] = kScale ? alpha * acc : acc;
   }
   __syncwarp();
+}
+__device__ __forceinline__ void warp_mm(double* Y, const double* X, int ldx, const double* Z, int ldz, int M, int N,
+                                        int K) {
+  warp_mm_t<false>(Y, X, ldx, Z, ldz, M, N, K, 1.0);
+}
+__device__ __forceinline__ void warp_mm_scaled(double* Y, const double* X, int ldx, const double* Z, int ldz, int M,
+                                               int N, int K, double alpha) {
+  warp_mm_t<true>(Y, X, ldx, Z, ldz, M, N, K, alpha);
 }
 
 // warp copy of n contiguous doubles
@@ -688,13 +714,13 @@ __device__ void warp_contrib(const DevProb& P, const Job& J, int x, double (&acc
   switch (J.op) {
     case OP_LAM: {   // acc += w2 T^T (Lam T)
       warp_load(A, P.core64[k] + (long long)x * ra * rb, ra * rb);
-      warp_mm(Y, P.small + P.off_lam[k], ra, A, rb, ra, rb, ra, 1.0);
+      warp_mm(Y, P.small + P.off_lam[k], ra, A, rb, ra, rb, ra);
       acc_cols<NO>(acc, ia, ib, A, rb, Y, rb, ra, gpow(P, k, x, +1));
       break;
     }
     case OP_GAM: {   // acc += w2 (T Gam) T^T
       warp_load(A, P.core64[k] + (long long)x * ra * rb, ra * rb);
-      warp_mm(Y, A, rb, P.small + P.off_gam[k + 1], rb, ra, rb, rb, 1.0);
+      warp_mm(Y, A, rb, P.small + P.off_gam[k + 1], rb, ra, rb, rb);
       acc_rows<NO>(acc, ia, ib, Y, rb, A, rb, rb, gpow(P, k, x, +1));
       break;
     }
@@ -707,7 +733,7 @@ __device__ void warp_contrib(const DevProb& P, const Job& J, int x, double (&acc
     case OP_PSI: {   // acc += (C Psi) C^T
       const int qa = P.q[k], qb = P.q[k + 1];
       warp_load(A, P.C[k] + (long long)x * qa * qb, qa * qb);
-      warp_mm(Y, A, qb, P.small + P.off_psi[k + 1], qb, qa, qb, qb, 1.0);
+      warp_mm(Y, A, qb, P.small + P.off_psi[k + 1], qb, qa, qb, qb);
       acc_rows<NO>(acc, ia, ib, Y, qb, A, qb, qb, 1.0);
       break;
     }
@@ -717,7 +743,7 @@ __device__ void warp_contrib(const DevProb& P, const Job& J, int x, double (&acc
       if (k == 0) {
         acc_cols<NO>(acc, ia, ib, A, qb, A, qb, qa, 1.0);
       } else {
-        warp_mm(Y, P.small + P.off_sk[k - 1], qa, A, qb, ra, qb, qa, 1.0);
+        warp_mm(Y, P.small + P.off_sk[k - 1], qa, A, qb, ra, qb, qa);
         acc_cols<NO>(acc, ia, ib, Y, qb, Y, qb, ra, 1.0);
       }
       break;
@@ -738,12 +764,12 @@ __device__ void warp_slice_map(const DevProb& P, int k, int x, double* scr) {
   warp_load(A, P.C[k] + (long long)x * qa * qb, qa * qb);
   const double* Cp = A;
   if (k > 0) {
-    warp_mm(Y, P.small + P.off_sk[k - 1], qa, A, qb, ra, qb, qa, 1.0);
+    warp_mm(Y, P.small + P.off_sk[k - 1], qa, A, qb, ra, qb, qa);
     Cp = Y;
   }
   const double* Tn = Cp;
   if (k < m - 1) {
-    warp_mm(Z, Cp, qb, P.small + P.off_pk[k], rb, ra, rb, qb, 1.0);
+    warp_mm(Z, Cp, qb, P.small + P.off_pk[k], rb, ra, rb, qb);
     Tn = Z;
   }
   double* T = P.core64[k] + (long long)x * ra * rb;
@@ -761,12 +787,11 @@ __device__ void warp_slice_map(const DevProb& P, int k, int x, double* scr) {
 }
 
 template <int NO>
-__global__ void __launch_bounds__(kThreads) k_stage_w(const DevProb P, const Stage S) {
+__device__ __forceinline__ void stage_w_body(const DevProb& P, const Stage& S, int b) {
   extern __shared__ __align__(16) double sm[];
   __shared__ int am_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* scr = sm + warp * 3 * wscr_mat(P);
-  int b = blockIdx.x;
   for (int i = 0; i < S.nmap; ++i) {     // slice maps first, one slice per warp
     const int k = S.map_k[i];
     const int nbm = (P.n[k] + kWarpsW - 1) / kWarpsW;
@@ -831,12 +856,17 @@ __global__ void __launch_bounds__(kThreads) k_stage_w(const DevProb P, const Sta
   }
 }
 
+template <int NO>
+__global__ void __launch_bounds__(kThreads) k_stage_w(const DevProb P, const Stage S) {
+  stage_w_body<NO>(P, S, blockIdx.x);
+}
+
 // B_k(x) and the block core C_k(x), one slice per warp (same as k_build_C)
-__global__ void __launch_bounds__(kThreads) k_build_C_w(const DevProb P, int nslices) {
+__device__ __forceinline__ void build_C_w_body(const DevProb& P, int blk, int nslices) {
   extern __shared__ __align__(16) double sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* scr = sm + warp * 3 * wscr_mat(P);
-  int g = blockIdx.x * kWarpsW + warp;
+  int g = blk * kWarpsW + warp;
   if (g >= nslices) return;
   int k = 0;
   while (k < P.m - 1 && g >= P.n[k]) {
@@ -851,8 +881,8 @@ __global__ void __launch_bounds__(kThreads) k_build_C_w(const DevProb P, int nsl
   double* t1 = scr + wscr_mat(P);
   double* B = scr + 2 * wscr_mat(P);
   warp_load(Tt, P.core64[k] + (long long)x * ra * rb, ra * rb);
-  warp_mm(t1, P.small + P.off_lami[k], ra, P.E[k] + (long long)x * ra * rb, rb, ra, rb, ra, 1.0);
-  warp_mm(B, t1, rb, P.small + P.off_gami[k + 1], rb, ra, rb, rb, -alpha * wi);
+  warp_mm(t1, P.small + P.off_lami[k], ra, P.E[k] + (long long)x * ra * rb, rb, ra, rb, ra);
+  warp_mm_scaled(B, t1, rb, P.small + P.off_gami[k + 1], rb, ra, rb, rb, -alpha * wi);
   if (k + 1 < m) {
     const double* Q = P.small + P.off_qm[k];
     for (int e = lane; e < ra * rb; e += 32) {
@@ -879,7 +909,78 @@ __global__ void __launch_bounds__(kThreads) k_build_C_w(const DevProb P, int nsl
       else
         v = (b < rb) ? B[(a - ra) * rb + b] : Tt[(a - ra) * rb + (b - rb)];
     }
-    C[i] = v * ws;
+    C[i] = P.weighted_retraction ? v * ws : v;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_build_C_w(const DevProb P, int nslices) {
+  build_C_w_body(P, blockIdx.x, nslices);
+}
+
+// ---- batched dense stages ----------------------------------------------------
+// Members of a batch whose dense stage takes the warp-per-slice path and the
+// same stage sequence (same order m) run every stage as one launch: blocks
+// [base[p], base[p+1]) execute member p's stage with its own descriptor,
+// plan, counters and partials, so each member computes exactly what it
+// computes alone.  (With a launch per member and stage, the GPU's kernel
+// launch rate, not the work, limited a batched step.)
+
+__device__ __forceinline__ int find_member(const int* __restrict__ base, int nprob, int blk) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(base + mid) <= blk) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename X>
+__device__ __forceinline__ void stage_copy(const X* __restrict__ src, X* dst) {
+  static_assert(sizeof(X) % 8 == 0, "8-byte words");
+  const uint2* sp = reinterpret_cast<const uint2*>(src);
+  uint2* dp = reinterpret_cast<uint2*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(X) / 8); i += blockDim.x) dp[i] = __ldg(sp + i);
+}
+
+template <int NO>
+__global__ void __launch_bounds__(kThreads) k_stage_w_batch(const DevProb* __restrict__ probs,
+                                                            const Stage* __restrict__ stages,
+                                                            const int* __restrict__ base, int nprob) {
+  __shared__ __align__(16) DevProb Ps;
+  __shared__ __align__(16) Stage Ss;
+  const int p = find_member(base, nprob, blockIdx.x);
+  stage_copy(probs + p, &Ps);
+  stage_copy(stages + p, &Ss);
+  __syncthreads();
+  stage_w_body<NO>(Ps, Ss, blockIdx.x - __ldg(base + p));
+}
+
+__global__ void __launch_bounds__(kThreads) k_build_C_w_batch(const DevProb* __restrict__ probs,
+                                                              const int* __restrict__ base, int nprob) {
+  __shared__ __align__(16) DevProb Ps;
+  const int p = find_member(base, nprob, blockIdx.x);
+  stage_copy(probs + p, &Ps);
+  __syncthreads();
+  int nslices = 0;
+  for (int k = 0; k < Ps.m; ++k) nslices += Ps.n[k];
+  build_C_w_body(Ps, blockIdx.x - __ldg(base + p), nslices);
+}
+
+// the copy of the cores into prev64 (the step-change metric), kCopyBlocks
+// blocks per member
+constexpr int kCopyBlocks = 16;
+__global__ void __launch_bounds__(256) k_save_prev_batch(const DevProb* __restrict__ probs, int nprob) {
+  const int p = blockIdx.x / kCopyBlocks, lb = blockIdx.x - p * kCopyBlocks;
+  if (p >= nprob) return;
+  const DevProb& P = probs[p];
+  slice_weights(P, lb * (long long)blockDim.x + threadIdx.x, (long long)kCopyBlocks * blockDim.x);
+  const int m = P.m;
+  for (int k = 0; k < m; ++k) {
+    const long long cnt = (long long)P.n[k] * P.r[k] * P.r[k + 1];
+    const double* src = P.core64[k];
+    double* dst = P.prev64[k];
+    for (long long i = lb * (long long)blockDim.x + threadIdx.x; i < cnt; i += (long long)kCopyBlocks * blockDim.x)
+      dst[i] = src[i];
   }
 }
 
@@ -1045,6 +1146,7 @@ __global__ void __launch_bounds__(128) k_build_C(const DevProb P) {
 }
 
 __global__ void k_copy_cores(const DevProb P, int to_prev) {
+  if (to_prev) slice_weights(P, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
   long long tot = 0;
   for (int k = 0; k < P.m; ++k) tot += (long long)P.n[k] * P.r[k] * P.r[k + 1];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
@@ -1376,6 +1478,11 @@ int ttc_alloc_dense(ttc_ctx* c) {
       TTC_CUDA(cudaFuncSetAttribute(k_stage_w<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
       TTC_CUDA(cudaFuncSetAttribute(k_stage_w<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
       TTC_CUDA(cudaFuncSetAttribute(k_build_C_w, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+      TTC_CUDA(cudaFuncSetAttribute(k_stage_w_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+      TTC_CUDA(cudaFuncSetAttribute(k_stage_w_batch<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+      TTC_CUDA(cudaFuncSetAttribute(k_stage_w_batch<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+      TTC_CUDA(cudaFuncSetAttribute(k_stage_w_batch<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
+      TTC_CUDA(cudaFuncSetAttribute(k_build_C_w_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
       granted[dev] = pl.smem_warp;
     }
   }
@@ -1413,6 +1520,134 @@ int ttc_launch_dense(ttc_ctx* c) {
   c->nlaunch += 1;
   for (auto& S : pl.psi) TTC_TRY(run_stage(c, pl, S));
   for (auto& S : pl.sweep) TTC_TRY(run_stage(c, pl, S));
+  return TTC_OK;
+}
+
+// ---- batched dense stages (host) ----------------------------------------------
+struct DenseGroup {
+  int nprob = 0, m = 0;
+  DevProb* probs = nullptr;
+  std::vector<Stage*> stages;   // per stage of the sequence (gram, psi, sweep): one Stage per member
+  std::vector<int*> base;       // per stage: block prefix over the members
+  std::vector<int> blocks, no;
+  int* base_c = nullptr;        // rank-2r assembly
+  int blocks_c = 0;
+  size_t smem = 0, smem_c = 0;
+};
+
+bool ttc_dense_batchable(const ttc_ctx* c) { return plan_of(c).warp && !c->hp.steepest; }
+
+void ttc_dense_group_destroy(DenseGroup* g) {
+  if (!g) return;
+  cudaFree(g->probs);
+  for (auto* p : g->stages) cudaFree(p);
+  for (auto* p : g->base) cudaFree(p);
+  cudaFree(g->base_c);
+  delete g;
+}
+
+int ttc_dense_group_create(ttc_ctx* const* members, int count, DenseGroup** out) {
+  *out = nullptr;
+  if (count < 1) return TTC_EINVAL;
+  DenseGroup* g = new (std::nothrow) DenseGroup();
+  if (!g) return TTC_ENOMEM;
+  g->nprob = count;
+  g->m = members[0]->m;
+  std::vector<DevProb> descs;
+  std::vector<const Plan*> plans;
+  for (int i = 0; i < count; ++i) {
+    if (members[i]->m != g->m || !ttc_dense_batchable(members[i])) {
+      ttc_dense_group_destroy(g);
+      return TTC_EINVAL;
+    }
+    descs.push_back(members[i]->hp);
+    plans.push_back(&plan_of(members[i]));
+    g->smem = std::max(g->smem, plans.back()->smem_warp);
+  }
+  auto upload = [&](void** dst, const void* src, size_t bytes) {
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) ttc_record_cuda_error(e);
+    return e;
+  };
+  cudaError_t e = upload((void**)&g->probs, descs.data(), sizeof(DevProb) * count);
+  // the stage sequence: Gram chains (m-1), right Grams of the rank-2r TT (m-1), bonds and maps (m)
+  const int nst = 3 * g->m - 2;
+  for (int si = 0; si < nst && e == cudaSuccess; ++si) {
+    std::vector<Stage> st(count);
+    std::vector<int> base(1, 0);
+    int dd = 1;
+    for (int i = 0; i < count; ++i) {
+      const Plan& pl = *plans[i];
+      const Stage& S = si < g->m - 1 ? pl.gram[si] : si < 2 * g->m - 2 ? pl.psi[si - (g->m - 1)]
+                                                                    : pl.sweep[si - (2 * g->m - 2)];
+      st[i] = S;
+      int nb = 0;
+      for (int j = 0; j < S.nmap; ++j) nb += (int)((members[i]->n[S.map_k[j]] + kWarpsW - 1) / kWarpsW);
+      for (int j = 0; j < S.njob; ++j) {
+        nb += S.job[j].nb;
+        dd = std::max(dd, S.job[j].rows * S.job[j].cols);
+      }
+      base.push_back(base.back() + nb);
+    }
+    Stage* sd = nullptr;
+    int* bd = nullptr;
+    e = upload((void**)&sd, st.data(), sizeof(Stage) * count);
+    g->stages.push_back(sd);
+    if (e == cudaSuccess) e = upload((void**)&bd, base.data(), sizeof(int) * base.size());
+    g->base.push_back(bd);
+    g->blocks.push_back(base.back());
+    g->no.push_back((dd + 31) / 32);
+  }
+  if (e == cudaSuccess) {
+    std::vector<int> base(1, 0);
+    for (int i = 0; i < count; ++i) {
+      int nsl = 0;
+      for (int k = 0; k < g->m; ++k) nsl += (int)members[i]->n[k];
+      base.push_back(base.back() + (nsl + kWarpsW - 1) / kWarpsW);
+      g->smem_c = std::max(g->smem_c, sizeof(double) * (size_t)kWarpsW * 3 * wscr_mat_host(members[i]->hp));
+    }
+    e = upload((void**)&g->base_c, base.data(), sizeof(int) * base.size());
+    g->blocks_c = base.back();
+  }
+  if (e != cudaSuccess) {
+    ttc_dense_group_destroy(g);
+    return e == cudaErrorMemoryAllocation ? TTC_ENOMEM : TTC_ECUDA;
+  }
+  *out = g;
+  return TTC_OK;
+}
+
+// save-previous copy, Gram stages, rank-2r assembly, right Grams, bonds: one
+// launch each for all members of the group
+int ttc_dense_group_launch(const DenseGroup* g, cudaStream_t st, long long* kernels) {
+  long long n = 0;
+  k_save_prev_batch<<<g->nprob * kCopyBlocks, 256, 0, st>>>(g->probs, g->nprob);
+  TTC_CUDA(cudaGetLastError());
+  ++n;
+  auto stage = [&](int si) -> int {
+    const int no = g->no[si];
+    if (no <= 1)
+      k_stage_w_batch<1><<<g->blocks[si], kThreads, g->smem, st>>>(g->probs, g->stages[si], g->base[si], g->nprob);
+    else if (no <= 2)
+      k_stage_w_batch<2><<<g->blocks[si], kThreads, g->smem, st>>>(g->probs, g->stages[si], g->base[si], g->nprob);
+    else if (no <= 4)
+      k_stage_w_batch<4><<<g->blocks[si], kThreads, g->smem, st>>>(g->probs, g->stages[si], g->base[si], g->nprob);
+    else if (no <= 8)
+      k_stage_w_batch<8><<<g->blocks[si], kThreads, g->smem, st>>>(g->probs, g->stages[si], g->base[si], g->nprob);
+    else
+      return TTC_EUNSUPPORTED;
+    TTC_CUDA(cudaGetLastError());
+    ++n;
+    return TTC_OK;
+  };
+  const int m = g->m;
+  for (int si = 0; si < m - 1; ++si) TTC_TRY(stage(si));
+  k_build_C_w_batch<<<g->blocks_c, kThreads, g->smem_c, st>>>(g->probs, g->base_c, g->nprob);
+  TTC_CUDA(cudaGetLastError());
+  ++n;
+  for (int si = m - 1; si < 3 * m - 2; ++si) TTC_TRY(stage(si));
+  if (kernels) *kernels += n;
   return TTC_OK;
 }
 

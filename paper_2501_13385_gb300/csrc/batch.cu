@@ -31,8 +31,10 @@ struct ttc_batch {
     std::vector<int> idx;
   };
   std::vector<Group> groups;
-  std::vector<DenseGroup*> dense;   // batched dense stages (members grouped by order)
+  std::vector<DenseGroup*> dense;   // batched dense stages (members grouped by order, then chunked)
   std::vector<int> in_dense;        // per member: its dense group, or -1 (own graph branch)
+  std::vector<cudaStream_t> dstreams;   // dense groups after the first run on these, concurrently
+  std::vector<cudaEvent_t> djoins;
   cudaGraphExec_t exec = nullptr;
   long long kernels_per_step = 0;
   long long nlaunch = 0;
@@ -119,7 +121,12 @@ int build_groups(ttc_batch* b) {
     G.g.tab_rows = tb.back();
     b->groups.push_back(G);
   }
-  // members whose dense stages can be batched, grouped by order
+  // members whose dense stages can be batched, grouped by order and split
+  // into up to kDenseChunks chunks of at least kDenseChunkMin members whose
+  // stage sequences run on concurrent streams: a chunk's single-block
+  // retraction steps (latency-bound) then overlap another chunk's
+  // slice-parallel FP64 reductions (throughput-bound)
+  constexpr int kDenseChunks = 4, kDenseChunkMin = 8;
   b->in_dense.assign(b->members.size(), -1);
   std::vector<int> orders;
   for (auto* c : b->members)
@@ -132,14 +139,33 @@ int build_groups(ttc_batch* b) {
         mem.push_back(b->members[i]);
         at.push_back(i);
       }
-    DenseGroup* d = nullptr;
-    int s = ttc_dense_group_create(mem.data(), (int)mem.size(), &d);
-    if (s != TTC_OK) {
-      free_groups(b);
-      return s;
+    const int cnt = (int)mem.size();
+    const int nch = std::max(1, std::min(kDenseChunks, cnt / kDenseChunkMin));
+    for (int ch = 0; ch < nch; ++ch) {
+      const int lo = (int)((long long)cnt * ch / nch), hi = (int)((long long)cnt * (ch + 1) / nch);
+      DenseGroup* d = nullptr;
+      int s = ttc_dense_group_create(mem.data() + lo, hi - lo, &d);
+      if (s != TTC_OK) {
+        free_groups(b);
+        return s;
+      }
+      for (int i = lo; i < hi; ++i) b->in_dense[at[i]] = (int)b->dense.size();
+      b->dense.push_back(d);
     }
-    for (int i : at) b->in_dense[i] = (int)b->dense.size();
-    b->dense.push_back(d);
+  }
+  while (b->dstreams.size() + 1 < b->dense.size()) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      if (st) cudaStreamDestroy(st);
+      ttc_record_cuda_error(e);
+      free_groups(b);
+      return TTC_ECUDA;
+    }
+    b->dstreams.push_back(st);
+    b->djoins.push_back(ev);
   }
   return TTC_OK;
 }
@@ -181,8 +207,15 @@ int capture(ttc_batch* b) {
     }
   if (s == TTC_OK && e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
   long long dense_kernels = 0;
-  for (auto* d : b->dense)
-    if (s == TTC_OK && e == cudaSuccess) s = ttc_dense_group_launch(d, b->stream, &dense_kernels);
+  for (size_t i = 1; i < b->dense.size() && s == TTC_OK && e == cudaSuccess; ++i) {
+    cudaStream_t ds = b->dstreams[i - 1];
+    e = cudaStreamWaitEvent(ds, b->fork, 0);
+    if (e == cudaSuccess) s = ttc_dense_group_launch(b->dense[i], ds, &dense_kernels);
+    if (s == TTC_OK && e == cudaSuccess) e = cudaEventRecord(b->djoins[i - 1], ds);
+  }
+  if (!b->dense.empty() && s == TTC_OK && e == cudaSuccess) s = ttc_dense_group_launch(b->dense[0], b->stream, &dense_kernels);
+  for (size_t i = 1; i < b->dense.size() && s == TTC_OK && e == cudaSuccess; ++i)
+    e = cudaStreamWaitEvent(b->stream, b->djoins[i - 1], 0);
   for (size_t i = 0; i < b->members.size() && s == TTC_OK && e == cudaSuccess; ++i) {
     if (b->in_dense[i] >= 0) continue;   // its dense stages ran batched above
     ttc_ctx* c = b->members[i];
@@ -336,6 +369,8 @@ void ttc_batch_destroy(ttc_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   free_groups(b);
+  for (auto st : b->dstreams) cudaStreamDestroy(st);
+  for (auto ev : b->djoins) cudaEventDestroy(ev);
   if (b->fork) cudaEventDestroy(b->fork);
   ttc_fork_destroy(b->pfork);
   for (auto ev : b->joins)

@@ -285,6 +285,7 @@ int ttc_create(ttc_ctx** out, int d, const int64_t* n, const int32_t* r, const t
   P.R = c->rank_bucket;
   P.dstar = ovf ? 0 : dl;
   P.inv_min_n = 1.0 / (double)minn;
+  P.inv_2m = 1.0 / (2.0 * (double)d);
   if (c->opt.step_rule < 0 || c->opt.step_rule > 1 || c->opt.metric < 0 || c->opt.metric > 1 ||
       c->opt.retraction < 0 || c->opt.retraction > 1 || c->opt.precision < 0 || c->opt.precision > 2) {
     delete c;

@@ -31,6 +31,7 @@ struct DevProb {
   int cbits[TTC_MAXM];         // bits of mode k
   double p;                    // N / d*
   double inv_min_n;            // 1 / min_k n_k
+  double inv_2m;               // 1 / (2m)
   int keep_residual;           // write g[] in input order during the pass
   int steepest;                // step size by exact line search (Eq. (PRGD stepsize))
   int uniform;                 // G_{l,i} = I (RGD)

@@ -72,6 +72,14 @@ struct Stage {
   Job job[TTC_MAXM + 4];
 };
 
+// Outputs a warp-per-slice job computes: the Grams Lam, Gam, Psi and N are
+// symmetric, so only their upper triangles (row <= column, packed row by
+// row) are accumulated and mirrored; T^T E (OP_H) is computed whole.
+__host__ __device__ inline bool warp_job_sym(const Job& J) { return J.op != OP_H; }
+__host__ __device__ inline int warp_job_outputs(const Job& J) {
+  return warp_job_sym(J) ? J.rows * (J.rows + 1) / 2 : J.rows * J.cols;
+}
+
 constexpr int kThreads = 256;
 constexpr int kMaxIter = 32;          // subspace iterations per bond (then the exact eigensolver)
 constexpr double kMoveTol2 = 1e-28;   // squared subspace movement per basis vector at convergence
@@ -88,16 +96,23 @@ __device__ __forceinline__ double ipow_2m(double y, int two_m) {
   }
   return acc;
 }
-__device__ __forceinline__ double inv_root(double v, int m) {
+// c = 1/(2m) in FP64 (from the descriptor)
+__device__ __forceinline__ double inv_root(double v, int m, double c) {
   const int two_m = 2 * m;
-  // seed: v^{-1/(2m)} = 2^{-(e + log2 f)/(2m)} with v = f 2^e, split into an
-  // integer power of two (exact) and an FP32 power of two in [1, 2)
+  // seed: v^{-1/(2m)} = 2^{-(e + log2 f)/(2m)} with v = f 2^e and
+  // e = 2m q + rr (0 <= rr < 2m, integer division): 2^{-q}, built exactly
+  // from its exponent bits (|q| <= 512 for normal v), times the FP32 power
+  // 2^{-(rr + log2 f)/(2m)} of an argument in (-1, 1/(2m)]; relative error
+  // ~1e-7, FP64 rounding after the two Newton steps
   int e;
   const double f = frexp(v, &e);
-  const double t = -((double)e + (double)log2f((float)f)) / (double)two_m;
-  const double ti = floor(t);
-  double y = ldexp((double)exp2f((float)(t - ti)), (int)ti);
-  const double c = 1.0 / (double)two_m;
+  int q = e / two_m, rr = e - q * two_m;
+  if (rr < 0) {
+    rr += two_m;
+    q -= 1;
+  }
+  const float tf = -((float)rr + log2f((float)f)) * (float)c;
+  double y = (double)exp2f(tf) * __longlong_as_double((long long)(1023 - q) << 52);
   for (int it = 0; it < 2; ++it) y = y * fma(c, fma(-v, ipow_2m(y, two_m), 1.0), 1.0);
   return y;
 }
@@ -111,7 +126,7 @@ __device__ __forceinline__ void slice_weights(const DevProb& P, long long t, lon
   for (int k = 0; k < P.m; ++k) {
     for (long long x = t; x < P.n[k]; x += nt) {
       const double v = eps + P.s[k][x];
-      const double y = inv_root(v, P.m);                                  // v^{-1/(2m)}
+      const double y = inv_root(v, P.m, P.inv_2m);                        // v^{-1/(2m)}
       P.wt[k][2 * x] = v * ipow_2m(y, 2 * P.m - 1);                       // v^{1/(2m)} = v * y^{2m-1}
       P.wt[k][2 * x + 1] = y;
     }
@@ -809,22 +824,36 @@ __device__ __forceinline__ void stage_w_body(const DevProb& P, const Stage& S, i
   }
   const Job J = S.job[j];
   const int dd = J.rows * J.cols;
+  const bool sym = warp_job_sym(J);
+  const int nout = warp_job_outputs(J);
   double acc[NO];
   int ia[NO], ib[NO];
 #pragma unroll
   for (int u = 0; u < NO; ++u) {
     acc[u] = 0.0;
-    const int o = min(lane + 32 * u, dd - 1);
-    ia[u] = o / J.cols;
-    ib[u] = o - ia[u] * J.cols;
+    int o = min(lane + 32 * u, nout - 1);
+    if (sym) {             // packed upper triangle: row i holds rows - i entries
+      int i = 0;
+      while (o >= J.rows - i) {
+        o -= J.rows - i;
+        ++i;
+      }
+      ia[u] = i;
+      ib[u] = i + o;
+    } else {
+      ia[u] = o / J.cols;
+      ib[u] = o - ia[u] * J.cols;
+    }
   }
   const int stride = J.nb * kWarpsW;
   for (int x = b * kWarpsW + warp; x < P.n[J.k]; x += stride) warp_contrib<NO>(P, J, x, acc, ia, ib, scr);
   __syncthreads();                       // the scratch becomes the warp-sum area
 #pragma unroll
   for (int u = 0; u < NO; ++u) {
-    const int o = lane + 32 * u;
-    if (o < dd) sm[warp * dd + o] = acc[u];
+    if (lane + 32 * u < nout) {
+      sm[warp * dd + ia[u] * J.cols + ib[u]] = acc[u];
+      if (sym) sm[warp * dd + ib[u] * J.cols + ia[u]] = acc[u];
+    }
   }
   __syncthreads();
   double* out = P.red + J.red + (long long)b * dd;
@@ -1273,7 +1302,7 @@ int launch_stage_w(ttc_ctx* c, const Stage& S, size_t smem) {
   for (int i = 0; i < S.nmap; ++i) nb += (int)((c->n[S.map_k[i]] + kWarpsW - 1) / kWarpsW);
   for (int j = 0; j < S.njob; ++j) {
     nb += S.job[j].nb;
-    dd = std::max(dd, S.job[j].rows * S.job[j].cols);
+    dd = std::max(dd, warp_job_outputs(S.job[j]));
   }
   const int no = (dd + 31) / 32;
   if (no <= 1)
@@ -1586,7 +1615,7 @@ int ttc_dense_group_create(ttc_ctx* const* members, int count, DenseGroup** out)
       for (int j = 0; j < S.nmap; ++j) nb += (int)((members[i]->n[S.map_k[j]] + kWarpsW - 1) / kWarpsW);
       for (int j = 0; j < S.njob; ++j) {
         nb += S.job[j].nb;
-        dd = std::max(dd, S.job[j].rows * S.job[j].cols);
+        dd = std::max(dd, warp_job_outputs(S.job[j]));
       }
       base.push_back(base.back() + nb);
     }

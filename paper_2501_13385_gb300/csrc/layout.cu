@@ -107,6 +107,84 @@ __global__ void k_scan(int* __restrict__ a, long long n, int* __restrict__ total
   }
 }
 
+// Multi-block exclusive scan for long count arrays (the digit-major radix
+// counts hold 256 per tile): block sums of consecutive segments, a scan of
+// the block sums, then each block scans its segment from its offset.  Same
+// integers as k_scan; the single-block k_scan took ~0.1 ms per radix pass.
+constexpr int kScanThreads = 256;
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocksum(const int* __restrict__ a, long long n, long long L,
+                                                                long long* __restrict__ bsum) {
+  __shared__ long long sh[kScanThreads];
+  const long long b0 = blockIdx.x * L, e0 = min(n, b0 + L);
+  long long s = 0;
+  for (long long i = b0 + threadIdx.x; i < e0; i += kScanThreads) s += a[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kScanThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = sh[0];
+}
+
+// exclusive scan of nb <= 1024 block sums in place (one block of 1024)
+__global__ void __launch_bounds__(1024) k_scan_top(long long* __restrict__ bsum, int nb, int* __restrict__ total) {
+  __shared__ long long sh[1024];
+  const int t = threadIdx.x;
+  const long long v = t < nb ? bsum[t] : 0;
+  sh[t] = v;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const long long w = t >= o ? sh[t - o] : 0;
+    __syncthreads();
+    sh[t] += w;
+    __syncthreads();
+  }
+  if (t < nb) bsum[t] = sh[t] - v;
+  if (t == 1023 && total) *total = (int)sh[t];
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(int* __restrict__ a, long long n, long long L,
+                                                             const long long* __restrict__ bsum) {
+  __shared__ long long sh[kScanThreads];
+  __shared__ long long base;
+  const int t = threadIdx.x;
+  if (t == 0) base = bsum[blockIdx.x];
+  const long long b0 = blockIdx.x * L, e0 = min(n, b0 + L);
+  for (long long c0 = b0; c0 < e0; c0 += kScanThreads) {
+    const long long i = c0 + t;
+    const int v = i < e0 ? a[i] : 0;
+    sh[t] = v;
+    __syncthreads();
+    for (int o = 1; o < kScanThreads; o <<= 1) {
+      const long long w = t >= o ? sh[t - o] : 0;
+      __syncthreads();
+      sh[t] += w;
+      __syncthreads();
+    }
+    const long long incl = sh[t], bb = base;
+    __syncthreads();
+    if (i < e0) a[i] = (int)(bb + incl - v);
+    if (t == kScanThreads - 1) base = bb + incl;
+    __syncthreads();
+  }
+}
+
+// exclusive scan of a[0..n) in place; total (if given) receives the sum;
+// bsum: 1024 long longs of scratch
+void scan_ints(int* a, long long n, int* total, long long* bsum, cudaStream_t st) {
+  if (n <= 16384) {
+    k_scan<<<1, 1024, 0, st>>>(a, n, total);
+    return;
+  }
+  long long L = std::max(4096LL, (n + 1023) / 1024);
+  L = (L + kScanThreads - 1) / kScanThreads * kScanThreads;
+  const int nb = (int)((n + L - 1) / L);   // <= 1024
+  k_scan_blocksum<<<nb, kScanThreads, 0, st>>>(a, n, L, bsum);
+  k_scan_top<<<1, 1024, 0, st>>>(bsum, nb, total);
+  k_scan_apply<<<nb, kScanThreads, 0, st>>>(a, n, L, bsum);
+}
+
 __global__ void k_iota(int* __restrict__ p, int N) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < N) p[j] = j;
@@ -163,7 +241,7 @@ inline int nblk(long long n, int bs) { return (int)((n + bs - 1) / bs); }
 
 // stable LSD radix sort of perm_in by the coordinate of mode k (8-bit digits)
 int sort_by_mode(ttc_ctx* c, const uint32_t* code, int* perm_in, int* perm_out, int* tmp_perm, int k,
-                 int* counts) {
+                 int* counts, long long* bsum) {
   const DevProb& P = c->hp;
   int N = P.N;
   int ntiles = nblk(N, kTile);
@@ -182,7 +260,7 @@ int sort_by_mode(ttc_ctx* c, const uint32_t* code, int* perm_in, int* perm_out, 
     int shift = P.cshift[k] + 8 * ps;
     long long ncount = (long long)(1 << dbits) * ntiles;
     k_digit_hist<<<ntiles, kTile, 0, st>>>(src, code, P.W, N, P.cword[k], shift, dbits, ntiles, counts);
-    k_scan<<<1, 1024, 0, st>>>(counts, ncount, nullptr);
+    scan_ints(counts, ncount, nullptr, bsum, st);
     k_digit_scatter<<<ntiles, kTile, 0, st>>>(src, dst, code, P.W, N, P.cword[k], shift, dbits, ntiles, counts);
     TTC_CUDA(cudaGetLastError());
     src = dst;
@@ -222,13 +300,14 @@ int ttc_build_layout(ttc_ctx* c, const int32_t* idx_host, const double* y_host) 
   double* y_d = nullptr;
   uint32_t* code_in = nullptr;
   int *pa = nullptr, *pb = nullptr, *pt = nullptr, *counts = nullptr, *flags = nullptr, *scr = nullptr;
+  long long* bsum = nullptr;
   int ntiles = nblk(N, kTile);
   long long ncount_max = 256LL * ntiles;
   long long maxn = 0;
   for (int k = 0; k < m; ++k) maxn = std::max(maxn, c->n[k]);
   auto cleanup = [&]() {
     for (void* q : {(void*)idx_d, (void*)y_d, (void*)code_in, (void*)pa, (void*)pb, (void*)pt, (void*)counts,
-                    (void*)flags, (void*)scr})
+                    (void*)flags, (void*)scr, (void*)bsum})
       ttc_pool_free(q, st);
   };
 #define LTRY(call)                        \
@@ -247,7 +326,8 @@ int ttc_build_layout(ttc_ctx* c, const int32_t* idx_host, const double* y_host) 
   LTRY(ttc_pool_alloc((void**)&pb, sizeof(int) * (size_t)N, st));
   LTRY(ttc_pool_alloc((void**)&pt, sizeof(int) * (size_t)N, st));
   LTRY(ttc_pool_alloc((void**)&counts, sizeof(int) * (size_t)std::max(ncount_max, maxn + 2), st));
-  LTRY(ttc_pool_alloc((void**)&flags, sizeof(int) * 4, st));
+  LTRY(ttc_pool_alloc((void**)&flags, sizeof(int) * (4 + TTC_MAXM), st));   // flags, then per-mode chunk totals
+  LTRY(ttc_pool_alloc((void**)&bsum, sizeof(long long) * 1024, st));
   LTRY(ttc_pool_alloc((void**)&scr, sizeof(int) * (size_t)(maxn + 2), st));
   LTRY(cudaMemcpyAsync(idx_d, idx_host, sizeof(int32_t) * (size_t)N * m, cudaMemcpyHostToDevice, st));
   LTRY(cudaMemcpyAsync(y_d, y_host, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, st));
@@ -263,7 +343,7 @@ int ttc_build_layout(ttc_ctx* c, const int32_t* idx_host, const double* y_host) 
   // duplicates: lexicographic order by stable passes over modes m-1 .. 0
   k_iota<<<nblk(N, 256), 256, 0, st>>>(pa, N);
   for (int k = m - 1; k >= 0; --k) {
-    int s = sort_by_mode(c, code_in, pa, pb, pt, k, counts);
+    int s = sort_by_mode(c, code_in, pa, pb, pt, k, counts, bsum);
     if (s != TTC_OK) { cleanup(); return s; }
     std::swap(pa, pb);
   }
@@ -273,9 +353,11 @@ int ttc_build_layout(ttc_ctx* c, const int32_t* idx_host, const double* y_host) 
   LTRY(cudaStreamSynchronize(st));
   if (hflags & 2) { cleanup(); return TTC_EDUP; }
 
-  // per-mode layouts
+  // per-mode layouts; each mode's chunk list is allocated for its bound
+  // sum_x ceil(n_x / chunk) <= N / chunk + n_k, and the totals are read back
+  // once after all modes
   int maxstride = 1;
-  int base = 0;
+  int* totals = flags + 4;
   for (int k = 0; k < m; ++k) {
     int nk = (int)c->n[k];
     uint32_t* code_k = nullptr;
@@ -293,16 +375,14 @@ int ttc_build_layout(ttc_ctx* c, const int32_t* idx_host, const double* y_host) 
       return s;
     }
     k_iota<<<nblk(N, 256), 256, 0, st>>>(pa, N);
-    if ((s = sort_by_mode(c, code_in, pa, perm, pt, k, counts)) != TTC_OK) { cleanup(); return s; }
+    if ((s = sort_by_mode(c, code_in, pa, perm, pt, k, counts, bsum)) != TTC_OK) { cleanup(); return s; }
     k_gather_mode<<<nblk(N, 256), 256, 0, st>>>(perm, code_in, y_d, W, N, code_k, y32, y64);
     k_seg_bounds<<<nblk(N, 256), 256, 0, st>>>(perm, code_in, W, N, P.cword[k], P.cshift[k], P.cbits[k], nk, seg);
     k_chunk_counts<<<nblk(nk + 1, 256), 256, 0, st>>>(seg, nk, TTC_CHUNK, cfirst);
-    int total = 0;
-    k_scan<<<1, 1024, 0, st>>>(cfirst, nk + 1, flags + 1);
+    scan_ints(cfirst, nk + 1, totals + k, bsum, st);
     LTRY(cudaGetLastError());
-    LTRY(cudaMemcpyAsync(&total, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LTRY(cudaStreamSynchronize(st));
-    if ((s = ttc_alloc(c, (void**)&cseg, sizeof(int) * (size_t)std::max(total, 1), true)) != TTC_OK) {
+    const long long bound = (long long)N / TTC_CHUNK + nk + 1;
+    if ((s = ttc_alloc(c, (void**)&cseg, sizeof(int) * (size_t)bound, true)) != TTC_OK) {
       cleanup();
       return s;
     }
@@ -315,10 +395,16 @@ int ttc_build_layout(ttc_ctx* c, const int32_t* idx_host, const double* y_host) 
     P.seg[k] = seg;
     P.cfirst[k] = cfirst;
     P.cseg[k] = cseg;
-    P.nchunk[k] = total;
-    P.chunk_base[k] = base;
-    base += total;
     maxstride = std::max(maxstride, 1 + c->r[k] * c->r[k + 1]);
+  }
+  int htot[TTC_MAXM] = {0};
+  LTRY(cudaMemcpyAsync(htot, totals, sizeof(int) * m, cudaMemcpyDeviceToHost, st));
+  LTRY(cudaStreamSynchronize(st));
+  int base = 0;
+  for (int k = 0; k < m; ++k) {
+    P.nchunk[k] = htot[k];
+    P.chunk_base[k] = base;
+    base += htot[k];
   }
   P.chunk_base[m] = base;
   P.part_stride = maxstride;

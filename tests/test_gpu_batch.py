@@ -95,3 +95,33 @@ def test_contexts_of_different_ranks_coexist():
         assert np.array_equal(a, b)
     for c in (big, small, ref):
         c.close()
+
+
+def test_chunked_dense_stages_bitwise_equal_to_alone():
+    # 18 members of order 3 and 9 of order 4 on the warp-per-slice dense path:
+    # order 3 runs its dense stages as two concurrent chunks of 9 members,
+    # order 4 as one chunk; ranks, mode sizes and precisions differ inside
+    # each chunk
+    specs = []
+    for i in range(18):
+        specs.append((dict(n=[12 + i % 5, 9 + i % 3, 11], r=[1, 1 + i % 4, 2 + i % 3, 1], count=600 + 37 * i),
+                      ttc.PREC_FP32 if i % 2 else ttc.PREC_FP64))
+    for i in range(9):
+        specs.append((dict(n=[7, 6 + i % 2, 8, 5], r=[1, 2, 1 + i % 3, 2, 1], count=900 + 11 * i), ttc.PREC_FP32))
+    steps = 3
+    alone = []
+    for i, (spec, prec) in enumerate(specs):
+        P, c = make(spec, prec, 500 + i)
+        for _ in range(steps):
+            c.step()
+        alone.append(c.get_cores())
+        c.close()
+    ctxs = [make(spec, prec, 500 + i)[1] for i, (spec, prec) in enumerate(specs)]
+    with ttc.Batch(ctxs) as b:
+        for _ in range(steps):
+            b.step()
+        b.sync()
+    for c, ref in zip(ctxs, alone):
+        for a, r in zip(c.get_cores(), ref):
+            assert np.array_equal(a, r)
+        c.close()

@@ -205,9 +205,12 @@ int ttc_device_bytes(ttc_ctx* ctx, int64_t* bytes);
  * A batch steps many independent contexts together: one call enqueues one
  * PRGD iteration of every member as ONE CUDA graph launch.  The sampled pass
  * of all members that share a precision and rank bucket runs as one kernel
- * launch (blocks mapped to (member, chunk)), and the members' dense stages run
- * as parallel branches of the graph on their own streams.  Each member
- * computes exactly what it computes when stepped alone (bitwise).
+ * launch (blocks mapped to (member, chunk)).  The dense stages of members of
+ * the same order with TT-ranks <= 8 (and not the steepest step) run batched
+ * as well, one launch per stage for a chunk of members, with up to four
+ * chunks on concurrent streams; other members' dense stages run as parallel
+ * branches of the graph on their own streams.  Each member computes exactly
+ * what it computes when stepped alone (bitwise).
  * Members must have observations and cores set, must not be stepped on their
  * own while the batch is in use, and must not change their observations or
  * truth afterwards (create a new batch instead).  The batch does not own the

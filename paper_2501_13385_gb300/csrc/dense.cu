@@ -38,7 +38,12 @@
 //
 // Reductions over slices are split over blocks; the last block to finish sums
 // the block partials in block order (deterministic) and runs the small
-// factorization that follows, so each stage is one launch.
+// factorization that follows, so each stage is one launch.  The powers
+// G_k(x)^{+-1/(2m)} are computed once per step into a per-slice table by the
+// kernel that saves the previous cores, which runs after the slice reduction
+// (when eps is final) and before the first stage.  In a batch, members on the
+// warp-per-slice path run each stage as one launch over a chunk of members
+// (blocks mapped to members by prefix arrays).
 #include <algorithm>
 #include <cstring>
 #include <map>

@@ -169,3 +169,54 @@ def test_generators_shapes_and_spectrum():
     Q2 = w.planted_small(3)
     assert np.array_equal(Q.idx, Q2.idx) and np.array_equal(Q.y, Q2.y)
     assert w.feasible_ranks([4] * 12, 8) == [1, 4] + [8] * 9 + [4, 1]
+
+
+def test_tt_add_is_the_dense_sum():
+    # block cores of A + beta B (ranks add) against the dense sum
+    rng = np.random.default_rng(11)
+    for n, ra, rb in (([3, 4, 2], [1, 2, 3, 1], [1, 3, 1, 1]), ([5], [1, 1], [1, 1]), ([2, 3, 2, 2], [1, 2, 2, 2, 1], [1, 1, 2, 3, 1])):
+        a, b = rand_tt(rng, n, ra), rand_tt(rng, n, rb)
+        s = o.tt_add(a, b, -0.75)
+        assert [c.shape[0] for c in s[1:]] == [ra[k] + rb[k] for k in range(1, len(n))]
+        assert np.allclose(brute_full(s), brute_full(a) - 0.75 * brute_full(b), rtol=1e-13, atol=1e-13)
+
+
+def test_interface_rows_against_explicit_products():
+    # left and right interfaces of mode i for every entry, by explicit slice
+    # products in a Python loop; their sandwich of core i is the entry value
+    rng = np.random.default_rng(12)
+    n, r = [3, 2, 4, 3], [1, 2, 3, 2, 1]
+    cores = rand_tt(rng, n, r)
+    idx = np.array(list(itertools.product(*[range(d) for d in n])))[::5]
+    full = brute_full(cores)
+    for i in range(len(n)):
+        left, right = o.interface_rows(cores, idx, i)
+        for e, x in enumerate(idx):
+            lv = np.eye(1)
+            for k in range(i):
+                lv = lv @ cores[k][:, x[k], :]
+            rv = np.eye(1)
+            for k in range(len(n) - 1, i, -1):
+                rv = cores[k][:, x[k], :] @ rv
+            assert np.allclose(left[e], lv[0], rtol=1e-13, atol=1e-14)
+            assert np.allclose(right[e], rv[:, 0], rtol=1e-13, atol=1e-14)
+            assert math.isclose(left[e] @ cores[i][:, x[i], :] @ right[e], full[tuple(x)], rel_tol=1e-12, abs_tol=1e-13)
+
+
+def test_right_grams_are_sums_over_all_suffixes():
+    # Gam[k] = sum over every suffix multi-index x_{>k} of U^{>=k+1}(x) U^{>=k+1}(x)^T,
+    # enumerated by brute force (no recursion)
+    rng = np.random.default_rng(13)
+    n, r = [2, 3, 2, 3], [1, 2, 3, 2, 1]
+    cores = rand_tt(rng, n, r)
+    gam = o.right_grams(cores)
+    m = len(n)
+    assert np.array_equal(gam[m - 1], np.ones((1, 1)))
+    for k in range(m - 1):
+        G = np.zeros((r[k + 1], r[k + 1]))
+        for x in itertools.product(*[range(d) for d in n[k + 1:]]):
+            v = np.eye(r[k + 1])
+            for j, xj in enumerate(x):
+                v = v @ cores[k + 1 + j][:, xj, :]
+            G += v @ v.T
+        assert np.allclose(gam[k], G, rtol=1e-12, atol=1e-13)

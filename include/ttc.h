@@ -53,7 +53,9 @@ enum {
   TTC_PREC_MIXED = 1,  /* FP32 Omega pass (FP32 accumulate); FP64 dense stages;
                           ttc_solve switches the pass to FP64 once the relative
                           residual ||P_Omega(T_l - T*)|| / ||y|| falls below
-                          `polish_below` */
+                          `polish_below` or the stop metric falls below
+                          `polish_factor` times its tolerance; a MIXED solve
+                          reports convergence only at or after that switch */
   TTC_PREC_FP32 = 2    /* FP32 Omega pass only, never polished */
 };
 
@@ -99,6 +101,11 @@ typedef struct {
   int step_rule;        /* TTC_STEP_* */
   int metric;           /* TTC_METRIC_* */
   int retraction;       /* TTC_RETRACT_* */
+  double polish_factor; /* MIXED: also switch to FP64 once the stop metric is <= polish_factor * tol
+                           (near convergence; needed when noise keeps the residual from falling) */
+  int step_fallback;    /* nonzero (default): a solve with the constant step switches to the steepest
+                           step for its remaining iterations once the residual norm grows by more
+                           than 2x in one iteration (the constant's scale diverges on that problem) */
 } ttc_options;
 
 typedef struct {
@@ -106,7 +113,7 @@ typedef struct {
   double alpha;         /* alpha_l used */
   double res_norm;      /* ||P_Omega(T_l - T*)||_F before the step */
   int precision_used;   /* TTC_PREC_FP64 or TTC_PREC_FP32 for the Omega pass of this step */
-  int subspace_iters;   /* iterations the retraction's subspace solves took (all bonds) */
+  int subspace_iters;   /* Jacobi sweeps the retraction's bond SVDs took (all bonds) */
 } ttc_step_info;
 
 typedef struct {
@@ -115,11 +122,14 @@ typedef struct {
   double last_metric;   /* last value of the stop-rule metric */
   double res_norm;      /* residual norm at the last step */
   int polish_iter;      /* first FP64 iteration in MIXED mode (-1: none) */
+  int fallback_iter;    /* first iteration with the steepest step after a constant-step divergence
+                           (-1: none) */
 } ttc_solve_info;
 
 /* Fill `opt` with defaults: MIXED precision, eps_rel 1, alpha_scale 1.5,
  * tol 1e-6, max_iter 500, stop rule RELERR, check_every 1, polish_below 1e-5,
- * graphs on, constant step, preconditioned metric, plain retraction. */
+ * polish_factor 10, graphs on, constant step with the divergence fallback,
+ * preconditioned metric, plain retraction. */
 void ttc_default_options(ttc_options* opt);
 
 /* Create a context for order d (1 < d <= 16), mode sizes n[d] (n_k >= 1),

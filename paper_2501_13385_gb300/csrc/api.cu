@@ -121,6 +121,7 @@ int drop_graphs(ttc_ctx* c) {
 
 // the fixed launch sequence of one iteration
 int enqueue_iteration(ttc_ctx* c, int prec) {
+  c->hp.bond_fp64 = (prec == TTC_PREC_FP64) ? 1 : 0;   // FP64 steps refine the retraction's SVDs in FP64
   TTC_TRY(ttc_launch_omega_pass(c, prec));
   TTC_TRY(ttc_launch_save_prev(c));   // also the slice weights, which need this step's eps
   TTC_TRY(ttc_launch_dense(c));
@@ -216,6 +217,8 @@ void ttc_default_options(ttc_options* o) {
   o->stop_rule = TTC_STOP_RELERR;
   o->check_every = 1;
   o->polish_below = 1e-5;
+  o->polish_factor = 10.0;
+  o->step_fallback = 1;
   o->use_graph = 1;
   o->step_rule = TTC_STEP_CONSTANT;
   o->metric = TTC_METRIC_PRECOND;
@@ -505,6 +508,14 @@ void ttc_solve_begin(ttc_ctx* c, SolveState& st) {
   st.info.last_metric = -1.0;
   st.info.res_norm = -1.0;
   st.info.polish_iter = -1;
+  st.info.fallback_iter = -1;
+  st.prev_res = -1.0;
+  // every solve starts with the configured step rule (a previous solve may have fallen back)
+  const int steep = c->opt.step_rule == TTC_STEP_STEEPEST ? 1 : 0;
+  if (c->hp.steepest != steep) {
+    c->hp.steepest = steep;
+    c->graph_dirty = true;
+  }
   if (c->opt.precision == TTC_PREC_FP64) c->cur_prec = TTC_PREC_FP64;
   if (c->opt.precision == TTC_PREC_FP32 || c->opt.precision == TTC_PREC_MIXED) c->cur_prec = TTC_PREC_FP32;
 }
@@ -532,11 +543,16 @@ void ttc_solve_after(ttc_ctx* c, SolveState& st, const double* sc, bool checked)
     st.done = true;
     return;
   }
-  if (c->opt.precision == TTC_PREC_MIXED && c->cur_prec != TTC_PREC_FP64 && rel_res <= c->opt.polish_below) {
-    c->cur_prec = TTC_PREC_FP64;
-    st.info.polish_iter = st.it + 1;
+  // a constant step whose scale diverges on this problem shows as a growing
+  // residual: the remaining iterations take the steepest step (the exact line
+  // search of Eq. (PRGD stepsize)), which cannot increase f along the
+  // projected direction
+  if (c->opt.step_fallback && !c->hp.steepest && st.prev_res > 0.0 && rel_res > 2.0 * st.prev_res) {
+    c->hp.steepest = 1;
+    c->graph_dirty = true;
+    st.info.fallback_iter = st.it + 1;
   }
-  const bool polishing_done = (c->opt.precision != TTC_PREC_MIXED) || c->cur_prec == TTC_PREC_FP64;
+  st.prev_res = rel_res;
   if (checked && (c->opt.stop_rule == TTC_STOP_RELERR || c->opt.stop_rule == TTC_STOP_STEP) &&
       !(std::isfinite(sc[SC_METRIC]) && std::isfinite(sc[SC_NORM]))) {
     // the new iterate is not finite: never read that as convergence
@@ -554,6 +570,16 @@ void ttc_solve_after(ttc_ctx* c, SolveState& st, const double* sc, bool checked)
     metric = std::sqrt(std::fmax(sc[SC_METRIC], 0.0)) / std::fmax(1.0, std::sqrt(sc[SC_NORM]));
   }
   if (metric >= 0.0) st.info.last_metric = metric;
+  // MIXED: the pass switches to FP64 once the relative residual is small
+  // (noiseless data) or the stop metric is within polish_factor of its
+  // tolerance (near convergence; with noisy data the residual stays at the
+  // noise level and only this second test fires)
+  if (c->opt.precision == TTC_PREC_MIXED && c->cur_prec != TTC_PREC_FP64 &&
+      (rel_res <= c->opt.polish_below || (metric >= 0.0 && metric <= c->opt.polish_factor * c->opt.tol))) {
+    c->cur_prec = TTC_PREC_FP64;
+    st.info.polish_iter = st.it + 1;
+  }
+  const bool polishing_done = (c->opt.precision != TTC_PREC_MIXED) || c->cur_prec == TTC_PREC_FP64;
   if (metric >= 0.0 && metric <= c->opt.tol && polishing_done) {
     st.info.converged = 1;
     st.status = TTC_OK;

@@ -15,7 +15,7 @@
 
 struct ttc_batch {
   std::vector<ttc_ctx*> members;
-  std::vector<int> prec_at_capture;
+  std::vector<int> prec_at_capture;   // per member: 2 x pass precision + steepest-step flag
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   PassFork pfork;              // concurrent mode-class launches of the batched pass
@@ -175,9 +175,11 @@ int capture(ttc_batch* b) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
+  // the retraction refines its SVDs to FP64 accuracy in a member's FP64 steps
+  for (auto* c : b->members) c->hp.bond_fp64 = (c->cur_prec == TTC_PREC_FP64) ? 1 : 0;
   TTC_TRY(build_groups(b));
   b->prec_at_capture.clear();
-  for (auto* c : b->members) b->prec_at_capture.push_back(c->cur_prec);
+  for (auto* c : b->members) b->prec_at_capture.push_back(c->cur_prec * 2 + c->hp.steepest);
   std::vector<long long> before;
   for (auto* c : b->members) before.push_back(c->nlaunch);
   cudaGraph_t g = nullptr;
@@ -305,7 +307,7 @@ int ttc_batch_step(ttc_batch* b) {
   if (!b) return TTC_EINVAL;
   bool stale = (b->exec == nullptr);
   for (size_t i = 0; i < b->members.size() && !stale; ++i)
-    stale = (b->members[i]->cur_prec != b->prec_at_capture[i]);
+    stale = (b->members[i]->cur_prec * 2 + b->members[i]->hp.steepest != b->prec_at_capture[i]);
   if (stale) TTC_TRY(capture(b));
   TTC_CUDA(cudaGraphLaunch(b->exec, b->stream));
   b->nlaunch += b->kernels_per_step;

@@ -36,6 +36,7 @@ struct DevProb {
   int steepest;                // step size by exact line search (Eq. (PRGD stepsize))
   int uniform;                 // G_{l,i} = I (RGD)
   int weighted_retraction;     // Remark 3.6: W^{-1/2} SVD^tt_r W^{1/2}
+  int bond_fp64;               // this step's retraction refines its SVDs to FP64 accuracy (FP64 pass)
 
   // current iterate
   double* core64[TTC_MAXM];    // FP64 master, slice-major, unpadded
@@ -85,6 +86,7 @@ struct DevProb {
   double* wt[TTC_MAXM];          // this step's slice weights, n_k x 2: G_k(x)^{+1/(2m)}, G_k(x)^{-1/(2m)}
   double* E[TTC_MAXM];           // n_k x r_k x r_{k+1}
   double* B1[TTC_MAXM];          // steepest step: update cores at unit step, n_k x r_k x r_{k+1}
+  float* B1_32p[TTC_MAXM];       // the same in FP32, padded like core32p (FP32 steps evaluate with it)
   double* zw;                    // steepest step: per slice G^{1/(2m)} <Lam B1 Gam, B1> (all modes)
   double* tpart;                 // steepest step: block partials of ||P_Omega Z||^2
   double* g;                     // residual in input order (when keep_residual)
@@ -128,7 +130,7 @@ enum {
   SC_NORM = 7,      // reference norm^2 of the metric
   SC_EPS_REL = 8,
   SC_ALPHA_SCALE = 9,
-  SC_SUBIT = 10,    // subspace iterations of the retraction in the last iteration (all bonds)
+  SC_SUBIT = 10,    // Jacobi sweeps of the retraction's bond SVDs in the last iteration (all bonds)
   SC_COUNT = 16
 };
 

@@ -70,6 +70,7 @@ struct SolveState {
   int it = 0;
   int status = TTC_ENOTCONV;
   bool done = false;
+  double prev_res = -1.0;          // relative residual after the previous iteration (-1: none)
   ttc_solve_info info;
 };
 void ttc_solve_begin(ttc_ctx* c, SolveState& st);

@@ -25,8 +25,9 @@
 //      left singular vectors of (T^{<=k-1} (x) I)^T W^{<k>} = L(C'_k) C^{>=k+1}
 //      are L(C'_k) u for the dominant r-dimensional invariant subspace u of
 //      Psi[k+1] N_k (since M M^T L(C') u = L(C') Psi N u).  That subspace is
-//      found by subspace iteration started at the coordinates of the iterate's
-//      own part of the rank-2r cores, until the subspace moves by < 1e-14; the
+//      u = R_P^T w, w the top-r right singular vectors of G = R_N R_P^T
+//      (upper Cholesky factors N_k = R_N^T R_N, Psi[k+1] = R_P^T R_P), from a
+//      one-sided Jacobi SVD of G (FP32 sweeps, FP64 sweeps in FP64 steps); the
 //      new core is T_k(x) = C'_k(x) P_k with P_k = U R^{-1}, R^T R = U^T N_k U,
 //      so it is left-orthogonal; S_k = P_k^T N_k; the last core is S_{d-2} C_{d-1}.
 //      This is Algorithm 1 itself, not an approximation of it.
@@ -86,8 +87,6 @@ __host__ __device__ inline int warp_job_outputs(const Job& J) {
 }
 
 constexpr int kThreads = 256;
-constexpr int kMaxIter = 32;          // subspace iterations per bond (then the exact eigensolver)
-constexpr double kMoveTol2 = 1e-28;   // squared subspace movement per basis vector at convergence
 
 // y = v^{-1/(2m)} by Newton's iteration for inverse roots,
 // y <- y (1 + (1 - v y^{2m}) / (2m)), started from the FP32 power (relative
@@ -266,191 +265,141 @@ __device__ void post_small_proj(const DevProb& P, double* sm) {
   if (threadIdx.x == 0 && flag) atomicOr(P.flags, 2u);
 }
 
-// Orthonormal basis U of span(W) (q x r): FP32 CholeskyQR, repeated once if
-// needed, accepted when ||Z^T Z - I||_max < 1e-4 and then polished in FP64 by
-// Z (I - E/2 + 3E^2/8) (error O(E^3)); an FP64 Cholesky when the FP32 passes
-// cannot reach that (ill-conditioned W).  Scratch s: 2 q*r + 5 r*r doubles.
-__device__ void orthonormalize(const double* W, int q, int r, double* U, double* s, double* red, float* Lf,
-                               float* Lif, int* bad) {
-  const int tid = threadIdx.x;
-  __shared__ int pow2[1];
-  double* Z = s;
-  double* Z2 = Z + q * r;
-  double* G = Z2 + q * r;
-  double* E = G + r * r;
-  double* F = E + r * r;
-  double* Li = F + r * r;
-  double* work = Li + r * r;
-  const double* src = W;
-  for (int pass = 0; pass < 2; ++pass) {
-    blk_gemm<double>(r, r, q, src, r, true, src, r, false, G, r, 1.0, false);   // G = src^T src
-    __syncthreads();
-    if (tid < 32) warp_chol_inv32(G, r, r, Lf, Lif, &pow2[0]);
-    __syncthreads();
-    double* dst = (pass == 0) ? Z : Z2;
-    const double sc = ldexp(1.0, -pow2[0]);   // exact power of two
-    for (int i = tid; i < q * r; i += blockDim.x) {                               // dst = src L^{-T}
-      int a = i / r, c = i - (i / r) * r;
-      double acc = 0.0;
-      for (int t = 0; t <= c; ++t) acc = fma(src[a * r + t], (double)Lif[c * r + t], acc);
-      dst[i] = acc * sc;
-    }
-    __syncthreads();
-    blk_gemm<double>(r, r, q, dst, r, true, dst, r, false, E, r, 1.0, false);   // E = dst^T dst - I
-    __syncthreads();
-    double em = 0.0;
-    for (int i = tid; i < r * r; i += blockDim.x) {
-      double v = E[i] - (((i / r) == (i % r)) ? 1.0 : 0.0);
-      E[i] = v;
-      em = nanmax(em, fabs(v));
-    }
-    em = blk_max(em, red);
-    if (em < 1e-4) {   // polish: F = I - E/2 + 3/8 E^2, U = dst F
-      blk_gemm<double>(r, r, r, E, r, false, E, r, false, F, r, 0.375, false);
-      __syncthreads();
-      for (int i = tid; i < r * r; i += blockDim.x) F[i] += (((i / r) == (i % r)) ? 1.0 : 0.0) - 0.5 * E[i];
-      __syncthreads();
-      blk_gemm<double>(q, r, r, dst, r, false, F, r, false, U, r, 1.0, false);
-      __syncthreads();
-      return;
-    }
-    src = dst;
-  }
-  // FP64 Cholesky of W^T W
-  blk_gemm<double>(r, r, q, W, r, true, W, r, false, G, r, 1.0, false);
-  __syncthreads();
-  blk_chol_linv64(G, r, r, Li, work, bad);
-  for (int i = tid; i < q * r; i += blockDim.x) {
-    int a = i / r, c = i - (i / r) * r;
-    double acc = 0.0;
-    for (int t = 0; t <= c; ++t) acc = fma(W[a * r + t], Li[c * r + t], acc);
-    U[i] = acc;
-  }
-  __syncthreads();
-}
-
 // Bond k of the retraction: from N_k (in P.small) and Psi[k+1], P_k and S_k.
+// The top-r left singular vectors of (T^{<=k-1} (x) I)^T W^{<k>} =
+// L(C'_k) C^{>=k+1} are L(C'_k) u, u spanning the dominant r-dimensional
+// invariant subspace of Psi[k+1] N_k (M M^T L(C') u = L(C') Psi N u).  With
+// the upper Cholesky factors N_k = R_N^T R_N and Psi[k+1] = R_P^T R_P, the
+// matrix G = R_N R_P^T has G^T G = R_P N_k R_P^T, so u = R_P^T w for the
+// top-r right singular vectors w of G.  Those come from one-sided Jacobi on
+// G's columns: FP32 sweeps from the identity, then, when the step needs FP64
+// accuracy, FP64 sweeps on G V32 from the FP32 basis (quadratic convergence:
+// one or two sweeps).  Jacobi computes the whole SVD, so a small gap between
+// the r-th and (r+1)-th singular values costs no extra iterations.
 __device__ void post_bond(const DevProb& P, int k, double* sm) {
   const int q = P.q[k + 1], r = P.r[k + 1];
-  const int tid = threadIdx.x;
-  double* N = sm;                  // q x q
-  double* A = N + q * q;           // q x q : Psi N
-  double* U = A + q * q;           // q x r
-  double* W = U + q * r;           // q x r
-  double* V = W + q * r;           // q x r
-  double* Bm = V + q * r;          // r x r
-  double* scr = Bm + r * r;        // 2 q r + 5 r r
-  double* red = scr + 2 * q * r + 5 * r * r;   // blockDim
-  float* Lf = reinterpret_cast<float*>(red + blockDim.x);
-  float* Lif = Lf + r * r;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int qq = q * q;
+  double* N = sm;                  // q x q, unscaled (the normalisation below)
+  double* RP = N + qq;             // Psi (scaled) -> R_P
+  double* RN = RP + qq;            // N (scaled) -> R_N -> E -> G V (column-major)
+  double* GG = RN + qq;            // G (column-major) -> U, W
+  float* G32 = reinterpret_cast<float*>(GG + qq);   // q x q floats each, column-major
+  float* V32 = G32 + qq;
+  double* VD = GG + 2 * qq;        // the FP64 basis V (column-major)
+  double* red = VD + qq;           // blockDim doubles
+  double* dg = red + bd;           // 2q doubles
   __shared__ int bad;
+  __shared__ int order[TTC_MAXQ];
   __shared__ double scl[2];   // powers of two that scale Psi and N to unit size
-  for (int i = tid; i < q * q; i += blockDim.x) N[i] = P.small[P.off_nk[k] + i];
+  for (int i = tid; i < qq; i += bd) N[i] = P.small[P.off_nk[k] + i];
   if (tid == 0) bad = 0;
   __syncthreads();
-  {
-    // A = Psi N from operands scaled by powers of two to unit size: its
-    // invariant subspaces do not depend on the scale, and Psi N itself grows
-    // with the fourth power of the iterate's entries
-    // (both are SPD Grams: the largest entry is on the diagonal)
-    const double* Psi = P.small + P.off_psi[k + 1];
-    if (tid < 32) {
-      double mp = 0.0, mn = 0.0;
-      for (int i = tid; i < q; i += 32) {
-        mp = nanmax(mp, fabs(Psi[i * q + i]));
-        mn = nanmax(mn, fabs(N[i * q + i]));
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        mp = nanmax(mp, __shfl_xor_sync(0xffffffffu, mp, o));
-        mn = nanmax(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      }
-      if (tid == 0) {
-        int ep = 0, en = 0;
-        if (mp > 0.0 && mp <= 1.7e308) frexp(mp, &ep);
-        if (mn > 0.0 && mn <= 1.7e308) frexp(mn, &en);
-        scl[0] = ldexp(1.0, -ep);
-        scl[1] = ldexp(1.0, -en);
-      }
+  const double* Psi = P.small + P.off_psi[k + 1];
+  if (tid < 32) {
+    // both are PSD Grams: the largest entry is on the diagonal
+    double mp = 0.0, mn = 0.0;
+    for (int i = tid; i < q; i += 32) {
+      mp = nanmax(mp, fabs(Psi[i * q + i]));
+      mn = nanmax(mn, fabs(N[i * q + i]));
     }
-    __syncthreads();
-    double* Ps = scr;   // q*q <= 2 q r
-    double* Ns = W;     // W and V: 2 q r >= q*q doubles
-    for (int i = tid; i < q * q; i += blockDim.x) {
-      Ps[i] = Psi[i] * scl[0];
-      Ns[i] = N[i] * scl[1];
+    for (int o = 16; o > 0; o >>= 1) {
+      mp = nanmax(mp, __shfl_xor_sync(0xffffffffu, mp, o));
+      mn = nanmax(mn, __shfl_xor_sync(0xffffffffu, mn, o));
     }
-    __syncthreads();
-    blk_gemm<double>(q, q, q, Ps, q, false, Ns, q, false, A, q, 1.0, false);
-  }
-  // start: the coordinates of the iterate's own part (last r of the 2r bond)
-  for (int i = tid; i < q * r; i += blockDim.x) {
-    int a = i / r, c = i - (i / r) * r;
-    U[i] = (a == q - r + c) ? 1.0 : 0.0;
+    if (tid == 0) {
+      int ep = 0, en = 0;
+      if (mp > 0.0 && mp <= 1.7e308) frexp(mp, &ep);
+      if (mn > 0.0 && mn <= 1.7e308) frexp(mn, &en);
+      scl[0] = ldexp(1.0, -ep);
+      scl[1] = ldexp(1.0, -en);
+    }
   }
   __syncthreads();
-  int it = 0;
-  for (; it < kMaxIter; ++it) {
-    blk_gemm<double>(q, r, q, A, q, false, U, r, false, W, r, 1.0, false);       // W = A U
-    __syncthreads();
-    orthonormalize(W, q, r, V, scr, red, Lf, Lif, &bad);                         // V = orth(W)
-    blk_gemm<double>(r, r, q, U, r, true, V, r, false, Bm, r, 1.0, false);       // Bm = U^T V
-    __syncthreads();
-    double dd = 0.0;
-    for (int i = tid; i < q * r; i += blockDim.x) {                               // movement V - U Bm
-      int a = i / r, c = i - (i / r) * r;
-      double acc = V[i];
-      for (int t = 0; t < r; ++t) acc = fma(-U[a * r + t], Bm[t * r + c], acc);
-      dd = fma(acc, acc, dd);
-    }
-    double mv = blk_sum(dd, red);
-    for (int i = tid; i < q * r; i += blockDim.x) U[i] = V[i];
-    __syncthreads();
-    if (mv <= kMoveTol2 * r) {
-      ++it;
-      break;
-    }
+  for (int i = tid; i < qq; i += bd) {
+    RP[i] = Psi[i] * scl[0];
+    RN[i] = N[i] * scl[1];
   }
-  if (it == kMaxIter) {
-    // The subspace did not settle (a near tie of the r-th and (r+1)-th
-    // singular values at this bond): take it exactly from symmetric
-    // eigendecompositions of the scaled operators, Psi = Q diag(d) Q^T,
-    // S = Psi^{1/2}, M = S N S = V diag(w) V^T; then Psi N (S V) = (S V) diag(w),
-    // so the top r columns of S V span the invariant subspace.
-    const double* Psi = P.small + P.off_psi[k + 1];
-    double* X1 = A;                 // N stays; the regions after it are free now
-    double* Q = X1 + q * q;
-    double* dv = Q + q * q;
-    double* T1 = dv + q;
-    double* wk = T1 + q * q;        // q*q + 448 doubles for the Jacobi solver
-    for (int i = tid; i < q * q; i += blockDim.x) X1[i] = Psi[i] * scl[0];
-    __syncthreads();
-    blk_sym_eig(X1, q, Q, dv, wk);
-    for (int i = tid; i < q * q; i += blockDim.x) {                                // S = Q diag(sqrt d) Q^T
-      const int a = i / q, b = i - (i / q) * q;
-      double acc = 0.0;
-      for (int t = 0; t < q; ++t) acc = fma(Q[a * q + t] * sqrt(fmax(dv[t], 0.0)), Q[b * q + t], acc);
-      X1[i] = acc;
-    }
-    __syncthreads();
-    for (int i = tid; i < q * q; i += blockDim.x) {                                // T1 = (N scaled) S
-      const int a = i / q, b = i - (i / q) * q;
-      double acc = 0.0;
-      for (int t = 0; t < q; ++t) acc = fma(N[a * q + t] * scl[1], X1[t * q + b], acc);
-      T1[i] = acc;
-    }
-    __syncthreads();
-    blk_gemm<double>(q, q, q, X1, q, false, T1, q, false, Q, q, 1.0, false);      // M = S T1
-    __syncthreads();
-    blk_sym_eig(Q, q, T1, dv, wk);                                                 // V (descending) into T1
-    for (int i = tid; i < q * r; i += blockDim.x) {                                // W = S V[:, :r]
-      const int a = i / r, c = i - (i / r) * r;
-      double acc = 0.0;
-      for (int t = 0; t < q; ++t) acc = fma(X1[a * q + t], T1[t * q + c], acc);
-      W[i] = acc;
-    }
-    __syncthreads();
-    orthonormalize(W, q, r, U, scr, red, Lf, Lif, &bad);
+  blk_chol2_upper_psd(RN, RP, q, dg);
+  // G = R_N R_P^T, column-major: G[i][j] = sum_{t >= max(i, j)} R_N[i][t] R_P[j][t]
+  for (int idx = tid; idx < qq; idx += bd) {
+    const int j = idx / q, i = idx - j * q;
+    double acc = 0.0;
+    for (int t = max(i, j); t < q; ++t) acc = fma(RN[i * q + t], RP[j * q + t], acc);
+    GG[idx] = acc;
+    G32[idx] = (float)acc;
+    V32[idx] = (i == j) ? 1.f : 0.f;
   }
+  int sweeps = blk_hestenes<float>(G32, V32, q, 1e-6f, 24);
+  const bool fp64 = P.bond_fp64 != 0;
+  if (fp64) {
+    // V = V32 made orthonormal in FP64, V (I - E/2 + 3 E^2 / 8) with
+    // E = V32^T V32 - I (error O(|E|^3)); then FP64 sweeps on G V
+    __syncthreads();
+    for (int idx = tid; idx < qq; idx += bd) {     // E (R_N is not needed any more)
+      const int j = idx / q, i = idx - j * q;
+      double acc = (i == j) ? -1.0 : 0.0;
+      for (int t = 0; t < q; ++t) acc = fma((double)V32[i * q + t], (double)V32[j * q + t], acc);
+      RN[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < qq; idx += bd) {     // F = I - E/2 + 3/8 E^2 (into VD)
+      const int j = idx / q, i = idx - j * q;
+      double acc = 0.0;
+      for (int t = 0; t < q; ++t) acc = fma(RN[t * q + i], RN[j * q + t], acc);
+      VD[idx] = fma(0.375, acc, ((i == j) ? 1.0 : 0.0) - 0.5 * RN[idx]);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < qq; idx += bd) {     // V32 F (into RN: E is not needed any more)
+      const int j = idx / q, i = idx - j * q;
+      double acc = 0.0;
+      for (int t = 0; t < q; ++t) acc = fma((double)V32[t * q + i], VD[j * q + t], acc);
+      RN[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < qq; idx += bd) VD[idx] = RN[idx];   // V
+    __syncthreads();
+    for (int idx = tid; idx < qq; idx += bd) {     // G V (G is not needed afterwards)
+      const int j = idx / q, i = idx - j * q;
+      double acc = 0.0;
+      for (int t = 0; t < q; ++t) acc = fma(GG[t * q + i], VD[j * q + t], acc);
+      RN[idx] = acc;
+    }
+    sweeps += blk_hestenes<double>(RN, VD, q, 1e-14, 8);
+  }
+  __syncthreads();
+  // squared singular values (column norms), NaN ordered last
+  for (int j = tid; j < q; j += bd) {
+    double s2 = 0.0;
+    for (int i = 0; i < q; ++i) {
+      const double v = fp64 ? RN[j * q + i] : (double)G32[j * q + i];
+      s2 = fma(v, v, s2);
+    }
+    dg[j] = (s2 == s2) ? s2 : -1.0;
+  }
+  __syncthreads();
+  // descending order, ties by column index (a permutation for any input)
+  for (int j = tid; j < q; j += bd) {
+    int rk = 0;
+    for (int i = 0; i < q; ++i) rk += (dg[i] > dg[j]) || (dg[i] == dg[j] && i < j);
+    order[rk] = j;
+  }
+  __syncthreads();
+  // U = R_P^T w, w the top-r columns of V (q x r, row-major)
+  double* U = GG;
+  double* W = GG + q * r;
+  for (int idx = tid; idx < q * r; idx += bd) {
+    const int a = idx / r, c = idx - (idx / r) * r;
+    const int col = order[c];
+    double acc = 0.0;
+    for (int t = 0; t <= a; ++t) acc = fma(RP[t * q + a], fp64 ? VD[col * q + t] : (double)V32[col * q + t], acc);
+    U[idx] = acc;
+  }
+  __syncthreads();
+  double* Bm = GG + qq;            // r x r (over G32, V32 and VD, which are not needed any more)
+  double* scr = Bm + r * r;        // 5 r*r
+  float* Lf = reinterpret_cast<float*>(scr + 5 * r * r);
+  float* Lif = Lf + r * r;
   // normalisation: T_k = C' U R^{-1} with R^T R = G = U^T N U; R^{-1} from the
   // FP32 Cholesky of G checked by E = R^{-T} G R^{-1} - I (FP64 Cholesky when
   // ||E|| >= 1e-4), then polished: R^{-1} (I - E/2 + 3E^2/8)
@@ -506,7 +455,7 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
   __syncthreads();
   blk_gemm<double>(r, q, q, Pk, r, true, N, q, false, P.small + P.off_sk[k], q, 1.0, false);   // S = P^T N
   if (tid == 0 && bad) atomicOr(P.flags, 2u);
-  if (tid == 0) P.scal[SC_SUBIT] = (k == 0 ? 0.0 : P.scal[SC_SUBIT]) + (double)it;
+  if (tid == 0) P.scal[SC_SUBIT] = (k == 0 ? 0.0 : P.scal[SC_SUBIT]) + (double)sweeps;
 }
 
 // new core k: T_k(x) = S_{k-1} C_k(x) P_k  (no P for the last core)
@@ -1049,7 +998,11 @@ __global__ void __launch_bounds__(128) k_build_B1(const DevProb P) {
     __syncthreads();
   }
   double* out = P.B1[k] + (long long)x * ra * rb;
-  for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) out[i] = B[i];
+  float* out32 = P.B1_32p[k] + (long long)x * P.R * P.R;
+  for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
+    out[i] = B[i];
+    out32[pad_idx(P, k, i / rb, i - (i / rb) * rb)] = (float)B[i];
+  }
   blk_gemm<double>(ra, rb, ra, P.small + P.off_lam[k], ra, false, B, rb, false, t1, rb, 1.0, false);   // Lam B1
   __syncthreads();
   const double* Gm = P.small + P.off_gam[k + 1];
@@ -1114,6 +1067,101 @@ __global__ void __launch_bounds__(kTanThreads) k_tangent_sq(const DevProb P, int
       }
     }
     acc = fma(lZ[0], lZ[0], acc);
+  }
+  const double tot = blk_sum(acc, red);
+  if (threadIdx.x == 0) P.tpart[blockIdx.x] = tot;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(P.counters + kTanCounter, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  double den = 0.0, num = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += kTanThreads) den += __ldcg(P.tpart + i);
+  den = blk_sum(den, red);
+  for (int i = threadIdx.x; i < nslices; i += kTanThreads) num += __ldcg(P.zw + i);
+  num = blk_sum(num, red);
+  if (threadIdx.x == 0) {
+    if (!(P.scal[SC_ALPHA_OVR] > 0.0)) P.scal[SC_ALPHA] = den > 0.0 ? num / den : 0.0;
+    P.counters[kTanCounter] = 0;
+  }
+}
+
+// The same sum in an FP32 step: the chain in FP32 on the padded FP32 mirrors
+// of the cores and of B1 (rows of R floats, read as 16-byte vectors), the
+// squares summed in FP64.  The step size only scales the step, so FP32's
+// relative error (~1e-6) in alpha moves the iterate by that fraction of one
+// step, as the FP32 sampled pass does.
+template <int R>
+__global__ void __launch_bounds__(kTanThreads) k_tangent_sq32(const DevProb P, int nslices) {
+  __shared__ double red[kTanThreads];
+  __shared__ int am_last;
+  double acc = 0.0;
+  for (int e = blockIdx.x * kTanThreads + threadIdx.x; e < P.N; e += gridDim.x * kTanThreads) {
+    const Code w = load_code(P, 0, e);
+    float lT[R], lZ[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      lT[a] = 0.f;
+      lZ[a] = 0.f;
+    }
+    lT[0] = 1.f;
+    for (int k = 0; k < P.m; ++k) {
+      const int x = code_coord(P, w, k);
+      const int ra = P.r[k], rb = P.r[k + 1];
+      const float* S = P.core32p[k] + (long long)x * R * R;
+      const float* Bk = P.B1_32p[k] + (long long)x * R * R;
+      if (rb == 1) {   // the slice is one contiguous column
+        float t = 0.f, z = 0.f;
+#pragma unroll
+        for (int a0 = 0; a0 < R; a0 += 4) {
+          if (a0 >= ra) break;
+          const float4 sv = __ldg(reinterpret_cast<const float4*>(S + a0));
+          const float4 bv = __ldg(reinterpret_cast<const float4*>(Bk + a0));
+          const float s4[4] = {sv.x, sv.y, sv.z, sv.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            t = fmaf(lT[a0 + i], s4[i], t);
+            z = fmaf(lZ[a0 + i], s4[i], fmaf(lT[a0 + i], b4[i], z));
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+          lT[b] = b == 0 ? t : 0.f;
+          lZ[b] = b == 0 ? z : 0.f;
+        }
+      } else {
+        float nT[R], nZ[R];
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+          nT[b] = 0.f;
+          nZ[b] = 0.f;
+        }
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+          if (a >= ra) break;
+          const float la = lT[a], za = lZ[a];
+#pragma unroll
+          for (int b0 = 0; b0 < R; b0 += 4) {
+            if (b0 >= rb) break;
+            const float4 sv = __ldg(reinterpret_cast<const float4*>(S + a * R + b0));
+            const float4 bv = __ldg(reinterpret_cast<const float4*>(Bk + a * R + b0));
+            const float s4[4] = {sv.x, sv.y, sv.z, sv.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              nT[b0 + i] = fmaf(la, s4[i], nT[b0 + i]);
+              nZ[b0 + i] = fmaf(za, s4[i], fmaf(la, b4[i], nZ[b0 + i]));
+            }
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+          lT[b] = nT[b];
+          lZ[b] = nZ[b];
+        }
+      }
+    }
+    acc = fma((double)lZ[0], (double)lZ[0], acc);
   }
   const double tot = blk_sum(acc, red);
   if (threadIdx.x == 0) P.tpart[blockIdx.x] = tot;
@@ -1379,12 +1427,17 @@ int ttc_alloc_dense(ttc_ctx* c) {
     TTC_TRY(ttc_alloc(c, (void**)&pv, sizeof(double) * (size_t)c->n[k] * c->r[k] * c->r[k + 1], false));
     P.prev64[k] = pv;
   }
-  if (P.steepest) {
+  {   // the steepest step's buffers (also for the constant step, which may fall back to it)
     long long nsl = 0;
     for (int k = 0; k < m; ++k) {
       double* b1 = nullptr;
       TTC_TRY(ttc_alloc(c, (void**)&b1, sizeof(double) * (size_t)c->n[k] * c->r[k] * c->r[k + 1], false));
       P.B1[k] = b1;
+      float* b32 = nullptr;
+      const size_t padcnt = (size_t)c->n[k] * c->rank_bucket * c->rank_bucket;
+      TTC_TRY(ttc_alloc(c, (void**)&b32, sizeof(float) * padcnt, false));
+      TTC_CUDA(cudaMemsetAsync(b32, 0, sizeof(float) * padcnt, c->stream));   // the padding stays zero
+      P.B1_32p[k] = b32;
       nsl += c->n[k];
     }
     TTC_TRY(ttc_alloc(c, (void**)&P.zw, sizeof(double) * (size_t)nsl, false));
@@ -1489,10 +1542,9 @@ int ttc_alloc_dense(ttc_ctx* c) {
   size_t red_need = sizeof(double) * (size_t)(2 * qmax * qmax);
   red_need = std::max(red_need, sizeof(double) * (size_t)(2 * TTC_MAXR * TTC_MAXR));
   size_t proj_need = sizeof(double) * (size_t)(8 * 2 * rmax * rmax) + sizeof(float) * (size_t)(8 * 2 * rmax * rmax);
-  size_t bond_need = sizeof(double) * (size_t)(2 * qmax * qmax + 5 * qmax * rmax + 6 * rmax * rmax + kThreads) +
-                     sizeof(float) * (size_t)(2 * rmax * rmax);
-  // the bond's exact fallback: N, then 4 q^2 + q doubles plus the Jacobi solver's 448
-  bond_need = std::max(bond_need, sizeof(double) * (size_t)(5 * qmax * qmax + qmax + 448 + kThreads));
+  // the bond: N, the two factors, G, the FP32 pair G32 / V32, the FP64 basis (6 q^2 doubles), the
+  // block's reduction slots and the factor diagonals
+  size_t bond_need = sizeof(double) * (size_t)(6 * qmax * qmax + kThreads + 2 * qmax);
   pl.smem_stage = std::max(red_need, std::max(proj_need, bond_need)) + 64;
   pl.smem_warp = pl.warp ? std::max(pl.smem_stage, sizeof(double) * (size_t)kWarpsW * 3 * wscr_mat_host(P))
                          : pl.smem_stage;
@@ -1536,11 +1588,20 @@ int ttc_launch_dense(ttc_ctx* c) {
     k_build_B1<<<nslices, 128, 0, st>>>(P);
     TTC_CUDA(cudaGetLastError());
     const int tb = tangent_blocks(P);
-    switch (c->rank_bucket) {
-      case 4: k_tangent_sq<4><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
-      case 8: k_tangent_sq<8><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
-      case 16: k_tangent_sq<16><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
-      default: k_tangent_sq<32><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+    if (P.bond_fp64) {   // an FP64 step: ||P_Omega Z||^2 in FP64
+      switch (c->rank_bucket) {
+        case 4: k_tangent_sq<4><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+        case 8: k_tangent_sq<8><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+        case 16: k_tangent_sq<16><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+        default: k_tangent_sq<32><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+      }
+    } else {
+      switch (c->rank_bucket) {
+        case 4: k_tangent_sq32<4><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+        case 8: k_tangent_sq32<8><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+        case 16: k_tangent_sq32<16><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+        default: k_tangent_sq32<32><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+      }
     }
     TTC_CUDA(cudaGetLastError());
     c->nlaunch += 2;

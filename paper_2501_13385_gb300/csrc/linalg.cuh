@@ -1,7 +1,7 @@
-// Block-level small dense linear algebra in FP64 on shared-memory matrices:
-// deterministic block sums, SPD inverse by Cholesky, and the symmetric
-// eigendecomposition (cyclic Jacobi, round-robin parallel ordering) that the
-// retraction's truncated SVDs are built from.  Every routine must be called
+// Block-level small dense linear algebra on shared-memory matrices:
+// deterministic block sums, SPD inverse by Cholesky, semidefinite Cholesky
+// factors and the one-sided Jacobi SVD that the retraction's truncated SVDs
+// are built from.  Every routine must be called
 // by all threads of the block; matrices are row-major n x n with n <= 64.
 #pragma once
 #include "common.cuh"
@@ -76,105 +76,6 @@ static __device__ int blk_spd_inverse(double* A, int n, double* work, int* flag)
   for (int i = tid; i < n * n; i += bd) A[i] = work[i];
   __syncthreads();
   return *flag;
-}
-
-// A = V diag(w) V^T for symmetric A (destroyed).  Cyclic Jacobi: each sweep
-// runs n'-1 rounds (n' = n rounded up to even) of n'/2 disjoint rotations in
-// the round-robin (circle) order, every rotation zeroing its a_pq with
-// tan(phi) = sgn(theta) / (|theta| + sqrt(theta^2 + 1)),
-// theta = (a_qq - a_pp) / (2 a_pq).  Sweeps stop when the off-diagonal mass
-// is below 1e-30 of the total.  Eigenvalues sorted descending.
-// work: n*n + 4*TTC_MAXQ + blockDim.x doubles.
-static __device__ void blk_sym_eig(double* A, int n, double* V, double* w, double* work) {
-  const int tid = threadIdx.x, bd = blockDim.x;
-  const int n2 = n + (n & 1);
-  const int np = n2 / 2;
-  double* cs_c = work + n * n;
-  double* cs_s = cs_c + TTC_MAXQ;
-  int* pp = (int*)(cs_s + TTC_MAXQ);
-  int* qq = pp + TTC_MAXQ;
-  double* red = (double*)(qq + TTC_MAXQ);
-  for (int i = tid; i < n * n; i += bd) V[i] = (i / n == i % n) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int i = tid; i < n * n; i += bd) {
-      double a = A[i];
-      if (i / n != i % n) off += a * a;
-      tot += a * a;
-    }
-    off = blk_sum(off, red);
-    tot = blk_sum(tot, red);
-    if (off <= 1e-30 * tot || tot == 0.0) break;
-    for (int t = 0; t < n2 - 1; ++t) {
-      for (int i = tid; i < np; i += bd) {
-        int pa = (i == 0) ? 0 : ((i - 1 + t) % (n2 - 1)) + 1;
-        int posb = n2 - 1 - i;
-        int pb = ((posb - 1 + t) % (n2 - 1)) + 1;
-        int p = pa < pb ? pa : pb, q = pa < pb ? pb : pa;
-        double c = 1.0, s = 0.0;
-        if (q < n) {
-          double apq = A[p * n + q];
-          if (apq != 0.0) {
-            double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-            double tt = 1.0 / (fabs(theta) + sqrt(theta * theta + 1.0));
-            if (theta < 0) tt = -tt;
-            c = 1.0 / sqrt(tt * tt + 1.0);
-            s = tt * c;
-          }
-        }
-        cs_c[i] = c;
-        cs_s[i] = s;
-        pp[i] = p;
-        qq[i] = q;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < np * n; idx += bd) {   // rows p, q
-        int i = idx / n, j = idx % n;
-        int p = pp[i], q = qq[i];
-        if (q < n) {
-          double c = cs_c[i], s = cs_s[i];
-          double apj = A[p * n + j], aqj = A[q * n + j];
-          A[p * n + j] = c * apj - s * aqj;
-          A[q * n + j] = s * apj + c * aqj;
-        }
-      }
-      __syncthreads();
-      for (int idx = tid; idx < np * n; idx += bd) {   // columns p, q of A and V
-        int i = idx / n, j = idx % n;
-        int p = pp[i], q = qq[i];
-        if (q < n) {
-          double c = cs_c[i], s = cs_s[i];
-          double ajp = A[j * n + p], ajq = A[j * n + q];
-          A[j * n + p] = c * ajp - s * ajq;
-          A[j * n + q] = s * ajp + c * ajq;
-          double vjp = V[j * n + p], vjq = V[j * n + q];
-          V[j * n + p] = c * vjp - s * vjq;
-          V[j * n + q] = s * vjp + c * vjq;
-        }
-      }
-      __syncthreads();
-    }
-  }
-  // sort descending: order into pp (as ints), then permute V's columns
-  if (tid == 0) {
-    for (int i = 0; i < n; ++i) pp[i] = i;
-    for (int i = 0; i < n; ++i) {
-      int best = i;
-      for (int j = i + 1; j < n; ++j)
-        if (A[pp[j] * n + pp[j]] > A[pp[best] * n + pp[best]]) best = j;
-      int tmp = pp[i]; pp[i] = pp[best]; pp[best] = tmp;
-    }
-  }
-  __syncthreads();
-  for (int i = tid; i < n; i += bd) w[i] = A[pp[i] * n + pp[i]];
-  for (int idx = tid; idx < n * n; idx += bd) work[idx] = V[idx];
-  __syncthreads();
-  for (int idx = tid; idx < n * n; idx += bd) {
-    int j = idx / n, c = idx % n;
-    V[idx] = work[j * n + pp[c]];
-  }
-  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -355,4 +256,145 @@ static __device__ void blk_chol_linv64(const double* G, int ldg, int n, double* 
     }
   }
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Factors and SVDs for the retraction's bonds.
+// ---------------------------------------------------------------------------
+
+// Upper Cholesky factors of two symmetric positive semidefinite n x n
+// matrices (row-major, n <= 64) at once, in place: A = R_A^T R_A and
+// B = R_B^T R_B.  Right-looking, one pivot per barrier: the Schur complement
+// is updated whole (both triangles), so the update of pivot j reads column j
+// below the diagonal while row j is scaled into the factor.  A pivot at or
+// below 1e-14 of the largest diagonal entry is rounding noise of a
+// numerically singular Gram (its square root would turn noise of 1e-16 into
+// rows of size 1e-8): it gives a zero row, which keeps R^T R equal to the
+// matrix on its numerical range.  diag: 2n doubles.
+static __device__ void blk_chol2_upper_psd(double* A, double* B, int n, double* diag) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  __syncthreads();
+  double ma = 0.0, mb = 0.0;
+  for (int i = 0; i < n; ++i) {
+    ma = fmax(ma, A[i * n + i]);
+    mb = fmax(mb, B[i * n + i]);
+  }
+  const double ta = 1e-14 * ma, tb = 1e-14 * mb;
+  for (int j = 0; j < n; ++j) {
+    const double da = A[j * n + j], db = B[j * n + j];
+    const double ra = (da > ta) ? rsqrt(da) : 0.0;
+    const double rb = (db > tb) ? rsqrt(db) : 0.0;
+    const int t = n - 1 - j;
+    for (int idx = tid; idx < 2 * t * t; idx += bd) {
+      const bool second = idx >= t * t;
+      const int e = second ? idx - t * t : idx;
+      const int i = j + 1 + e / t, c = j + 1 + (e - (e / t) * t);
+      double* M = second ? B : A;
+      const double rr = second ? rb : ra;
+      M[i * n + c] = fma(-(M[i * n + j] * rr), M[c * n + j] * rr, M[i * n + c]);
+    }
+    for (int idx = tid; idx < 2 * t; idx += bd) {
+      const bool second = idx >= t;
+      const int c = j + 1 + (second ? idx - t : idx);
+      double* M = second ? B : A;
+      M[j * n + c] *= second ? rb : ra;
+    }
+    if (tid == 0) {
+      diag[j] = da * ra;        // sqrt(da), or 0
+      diag[n + j] = db * rb;
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < 2 * n * n; idx += bd) {
+    const bool second = idx >= n * n;
+    const int e = second ? idx - n * n : idx;
+    const int i = e / n, c = e - (e / n) * n;
+    double* M = second ? B : A;
+    if (c < i) M[e] = 0.0;
+    else if (c == i) M[e] = diag[(second ? n : 0) + i];
+  }
+  __syncthreads();
+}
+
+// One-sided (Hestenes) Jacobi: plane rotations of the columns of G (n x n,
+// n <= 64, column-major: column j at G + j*n) until they are mutually
+// orthogonal, so that G V = U diag(sigma), with the rotations accumulated in
+// V (column-major, enter with the starting basis).  A sweep is the
+// round-robin ordering: n' - 1 rounds (n' = n rounded up to even) of n'/2
+// disjoint pairs; each pair is handled by a group of lp lanes (4 for n <= 16,
+// else 8; a lane owns every lp-th row), so a block of 256 threads treats all
+// pairs of a round at once.  Pair (p, q) is rotated when
+// |g_p . g_q| > tol ||g_p|| ||g_q||, by the angle that zeroes the
+// off-diagonal of its 2 x 2 Gram [[a, c], [c, b]]:
+//   t = sgn(z) / (|z| + sqrt(1 + z^2)),  z = (b - a) / (2c),
+//   g_p <- cs g_p - sn g_q,  g_q <- sn g_p + cs g_q,  cs = 1/sqrt(1 + t^2), sn = t cs.
+// The sums of a pair are butterfly reductions over its lanes, identical on
+// every lane, so the lanes agree on the rotation.  Stops after a sweep
+// without rotations or after max_sweeps; returns the sweeps run.  The
+// rotations act on the factor, not on its Gram, so singular values of very
+// different sizes keep their relative accuracy.
+template <typename T>
+static __device__ int blk_hestenes(T* G, T* V, int n, T tol, int max_sweeps) {
+  const int lp = n <= 16 ? 4 : 8;
+  const int lane = threadIdx.x & 31;
+  const int slot = (threadIdx.x >> 5) * (32 / lp) + lane / lp;
+  const int nslots = (blockDim.x >> 5) * (32 / lp);
+  const int sub = lane & (lp - 1);
+  const int n2 = n + (n & 1), np = n2 / 2;
+  const int passes = (np + nslots - 1) / nslots;
+  __shared__ int rotated;
+  int sweep = 0;
+  while (sweep < max_sweeps) {
+    __syncthreads();
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int t = 0; t < n2 - 1; ++t) {
+      for (int pass = 0; pass < passes; ++pass) {
+        const int i = slot + pass * nslots;
+        int p = 0, q = 0;
+        bool act = false;
+        if (i < np) {
+          const int pa = (i == 0) ? 0 : ((i - 1 + t) % (n2 - 1)) + 1;
+          const int pb = ((n2 - 2 - i + t) % (n2 - 1)) + 1;
+          p = min(pa, pb);
+          q = max(pa, pb);
+          act = q < n;   // not the dummy column of an odd n
+        }
+        T al = T(0), be = T(0), ga = T(0);
+        if (act)
+          for (int row = sub; row < n; row += lp) {
+            const T a = G[p * n + row], b = G[q * n + row];
+            al = fma(a, a, al);
+            be = fma(b, b, be);
+            ga = fma(a, b, ga);
+          }
+        for (int o = lp / 2; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (act && fabs(ga) > tol * sqrt(al * be)) {
+          const T z = (be - al) / (T(2) * ga);
+          const T az = fabs(z);
+          const T tt = az > T(1e15) ? T(0.5) / z : copysign(T(1), z) / (az + sqrt(fma(z, z, T(1))));
+          const T cs = rsqrt(fma(tt, tt, T(1))), sn = cs * tt;
+          for (int row = sub; row < n; row += lp) {
+            const T a = G[p * n + row], b = G[q * n + row];
+            G[p * n + row] = fma(cs, a, -sn * b);
+            G[q * n + row] = fma(sn, a, cs * b);
+            const T x = V[p * n + row], y = V[q * n + row];
+            V[p * n + row] = fma(cs, x, -sn * y);
+            V[q * n + row] = fma(sn, x, cs * y);
+          }
+          if (sub == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    ++sweep;
+    const int any = rotated;
+    __syncthreads();
+    if (!any) break;
+  }
+  return sweep;
 }

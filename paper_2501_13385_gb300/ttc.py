@@ -42,7 +42,8 @@ class Options(C.Structure):
         ("precision", C.c_int), ("eps_rel", C.c_double), ("alpha_scale", C.c_double),
         ("eps_frozen", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("stop_rule", C.c_int),
         ("check_every", C.c_int), ("polish_below", C.c_double), ("use_graph", C.c_int),
-        ("step_rule", C.c_int), ("metric", C.c_int), ("retraction", C.c_int),
+        ("step_rule", C.c_int), ("metric", C.c_int), ("retraction", C.c_int), ("polish_factor", C.c_double),
+        ("step_fallback", C.c_int),
     ]
 
 
@@ -53,7 +54,7 @@ class StepInfo(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("converged", C.c_int), ("last_metric", C.c_double),
-                ("res_norm", C.c_double), ("polish_iter", C.c_int)]
+                ("res_norm", C.c_double), ("polish_iter", C.c_int), ("fallback_iter", C.c_int)]
 
 
 class Request(C.Structure):
@@ -260,7 +261,8 @@ class Context:
         if st not in (0, -6) or (raise_on_notconv and st == -6):
             _check(st, "ttc_solve")
         return {"status": STATUS.get(st, st), "iters": info.iters, "converged": bool(info.converged),
-                "last_metric": info.last_metric, "res_norm": info.res_norm, "polish_iter": info.polish_iter}
+                "last_metric": info.last_metric, "res_norm": info.res_norm, "polish_iter": info.polish_iter,
+                "fallback_iter": info.fallback_iter}
 
     def relerr(self) -> float:
         v = C.c_double()

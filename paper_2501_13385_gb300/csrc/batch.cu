@@ -24,7 +24,6 @@ struct ttc_batch {
   struct Group {
     BatchGroup g;
     DevProb* probs = nullptr;
-    int* pass_base = nullptr;
     int* pass_base_c = nullptr;   // three per-class prefix arrays, back to back
     int* seg_base = nullptr;
     long long* tab_base = nullptr;
@@ -52,7 +51,6 @@ void free_groups(ttc_batch* b) {
   b->in_dense.clear();
   for (auto& G : b->groups) {
     cudaFree(G.probs);
-    cudaFree(G.pass_base);
     cudaFree(G.pass_base_c);
     cudaFree(G.seg_base);
     cudaFree(G.tab_base);
@@ -71,7 +69,7 @@ int build_groups(ttc_batch* b) {
   for (auto& key : keys) {
     ttc_batch::Group G;
     std::vector<DevProb> descs;
-    std::vector<int> pb(1, 0), sb(1, 0);
+    std::vector<int> sb(1, 0);
     std::vector<int> pc[3] = {std::vector<int>(1, 0), std::vector<int>(1, 0), std::vector<int>(1, 0)};
     std::vector<long long> tb(1, 0);
     for (int i = 0; i < (int)b->members.size(); ++i) {
@@ -80,16 +78,13 @@ int build_groups(ttc_batch* b) {
       if (prec != key.first || c->rank_bucket != key.second) continue;
       G.idx.push_back(i);
       descs.push_back(c->hp);
-      pb.push_back(pb.back() + ttc_pass_blocks(c->hp, key.second));
       for (int cls = 0; cls < 3; ++cls) pc[cls].push_back(pc[cls].back() + ttc_pass_class_blocks(c->hp, cls));
       sb.push_back(sb.back() + ttc_seg_blocks(c->hp));
       tb.push_back(tb.back() + c->hp.tab_total);
     }
     cudaError_t e = cudaMalloc(&G.probs, sizeof(DevProb) * descs.size());
-    if (e == cudaSuccess) e = cudaMalloc(&G.pass_base, sizeof(int) * pb.size());
     if (e == cudaSuccess) e = cudaMalloc(&G.seg_base, sizeof(int) * sb.size());
     if (e == cudaSuccess) e = cudaMemcpy(G.probs, descs.data(), sizeof(DevProb) * descs.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(G.pass_base, pb.data(), sizeof(int) * pb.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(G.seg_base, sb.data(), sizeof(int) * sb.size(), cudaMemcpyHostToDevice);
     const size_t np1 = pc[0].size();
     if (e == cudaSuccess) e = cudaMalloc(&G.pass_base_c, sizeof(int) * 3 * np1);
@@ -109,10 +104,8 @@ int build_groups(ttc_batch* b) {
     for (int i : G.idx) G.g.RC = std::max(G.g.RC, b->members[i]->rank_max);
     G.g.nprob = (int)descs.size();
     G.g.probs = G.probs;
-    G.g.pass_base = G.pass_base;
     G.g.seg_base = G.seg_base;
     G.g.tab_base = G.tab_base;
-    G.g.pass_blocks = pb.back();
     for (int cls = 0; cls < 3; ++cls) {
       G.g.pass_base_c[cls] = G.pass_base_c + cls * np1;
       G.g.pass_blocks_c[cls] = pc[cls].back();
@@ -196,10 +189,7 @@ int capture(ttc_batch* b) {
   for (auto& G : b->groups)
     if (s == TTC_OK && e == cudaSuccess) {
       s = ttc_launch_omega_pass_batch(G.g, b->stream, 0, &b->pfork);
-      if (G.g.R <= 8)   // one launch per non-empty mode class
-        for (int cls = 0; cls < 3; ++cls) batched += G.g.pass_blocks_c[cls] > 0 ? 1 : 0;
-      else
-        ++batched;
+      for (int cls = 0; cls < 3; ++cls) batched += G.g.pass_blocks_c[cls] > 0 ? 1 : 0;   // one launch per class
     }
   if (b->prof && e == cudaSuccess) e = cudaEventRecordWithFlags(b->ev_end, b->stream, cudaEventRecordExternal);
   for (auto& G : b->groups)

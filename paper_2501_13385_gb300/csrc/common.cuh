@@ -108,6 +108,9 @@ struct DevProb {
   int off_mlam[3][TTC_MAXM + 1];  // metric Gram sweep: A^T A, A^T B, B^T B left Grams
   double* red;                   // partial sums of slice reductions
   long long red_metric;          // offset of the metric's partials in red
+  double* red2;                  // group partials of the dense stages' two-level reductions
+  long long red2_metric;         // offset of the metric's group partials in red2
+  int* gctr;                     // group counters of the two-level reductions
   double* scal;                  // scalars, see SC_* below
   unsigned* flags;               // = (unsigned*)(scal + SC_FLAGS): bit 0 non-finite, bit 1 lost rank
   int* counters;                 // completion counters of the fused reductions (reset by their last block)

@@ -98,20 +98,18 @@ struct BatchGroup {
   int R;
   int nprob;
   const DevProb* probs;      // device array of the members' descriptors
-  const int* pass_base;      // device [nprob + 1]: block offsets of the sampled pass
   const int* seg_base;       // device [nprob + 1]: block offsets of the slice reduction
   const long long* tab_base; // device [nprob + 1]: row offsets of the interface tables
   int RC;                    // register size of the pass: the members' largest TT-rank
   const int* pass_base_c[3]; // small ranks: block offsets per mode class (first, interior, last)
   int pass_blocks_c[3];
-  int pass_blocks, seg_blocks;
+  int seg_blocks;
   long long tab_rows;
 };
 
-// mode classes of the small-rank sampled pass (separate launches, each at its
-// own register budget): the first mode, the interior modes, the last mode;
-// PC_ALL is the large-rank pass over all chunks
-enum { PC_FIRST = 0, PC_MIDDLE = 1, PC_LAST = 2, PC_ALL = 3 };
+// mode classes of the sampled pass (separate launches, each at its own
+// register budget): the first mode, the interior modes, the last mode
+enum { PC_FIRST = 0, PC_MIDDLE = 1, PC_LAST = 2 };
 inline void ttc_pass_class_range(const DevProb& P, int cls, int* c0, int* c1) {
   if (cls == PC_FIRST) {
     *c0 = 0;
@@ -124,17 +122,14 @@ inline void ttc_pass_class_range(const DevProb& P, int cls, int* c0, int* c1) {
     *c1 = P.chunk_base[P.m - 1];
   }
 }
+// blocks of one class launch: one chunk per warp, except the interior modes
+// at large ranks (R >= 16), one chunk per block
 inline int ttc_pass_class_blocks(const DevProb& P, int cls) {
   int c0, c1;
   ttc_pass_class_range(P, cls, &c0, &c1);
-  return c1 > c0 ? (c1 - c0 + TTC_NT / 32 - 1) / (TTC_NT / 32) : 0;
-}
-
-// blocks of one sampled pass: small rank buckets (R <= 8) reduce one chunk
-// per warp, larger ones one chunk per block
-inline int ttc_pass_blocks(const DevProb& P, int R) {
-  const int chunks = P.chunk_base[P.m];
-  return R <= 8 ? (chunks + TTC_NT / 32 - 1) / (TTC_NT / 32) : chunks;
+  if (c1 <= c0) return 0;
+  if (P.R >= 16 && cls == PC_MIDDLE) return c1 - c0;
+  return (c1 - c0 + TTC_NT / 32 - 1) / (TTC_NT / 32);
 }
 
 // one launch of the sampled-pass kernel: a single problem (g == nullptr)
@@ -146,12 +141,13 @@ struct PassLaunch {
   const PassFork* fork;      // may be null: the class launches then run in sequence
 };
 // pass_small_f32.cu / pass_small_f64.cu: rank buckets 4 and 8, register size
-// RC = the largest TT-rank (1..8); pass_large.cu: buckets 16 and 32
+// RC = the largest TT-rank (1..8); pass_large.cu: buckets 16 and 32, RC 16,
+// 24 or 32 (the largest TT-rank rounded up to a multiple of 8)
 int ttc_pass_small_f32(int RC, const PassLaunch& L);
 int ttc_pass_small_f64(int RC, const PassLaunch& L);
 int ttc_pass_small_f32_r4(int RC, const PassLaunch& L);   // pass_small_f32_r4.cu: RC = 1..4
 int ttc_pass_small_f64_r4(int RC, const PassLaunch& L);   // pass_small_f64_r4.cu
-int ttc_pass_large(bool f32, int R, const PassLaunch& L);
+int ttc_pass_large(bool f32, int R, int RC, const PassLaunch& L);
 int ttc_pass_opt_in_large();
 
 // blocks of the slice reduction: one slice per warp, 8 per block

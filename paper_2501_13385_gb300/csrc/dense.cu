@@ -64,7 +64,8 @@ struct Job {
   int op, k;
   int nb;            // reduction blocks
   int rows, cols;    // output is rows x cols
-  long long red;     // offset in P.red of the partials
+  long long red;     // offset in P.red of the block partials
+  long long red2;    // offset in P.red2 of the group partials (groups of kGroup blocks)
   int dst;           // offset in P.small of the result
 };
 
@@ -145,7 +146,7 @@ __device__ __forceinline__ double gpow(const DevProb& P, int k, int x, int sign)
 
 // ---- per-slice contributions ------------------------------------------------
 __device__ void slice_contrib(const DevProb& P, const Stage& S, const Job& J, int x, double* acc, double* Y) {
-  const int k = J.k, m = P.m;
+  const int k = J.k;
   const int ra = P.r[k], rb = P.r[k + 1];
   const double* T = P.core64[k] + (long long)x * ra * rb;
   switch (J.op) {
@@ -284,11 +285,11 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
   double* RP = N + qq;             // Psi (scaled) -> R_P
   double* RN = RP + qq;            // N (scaled) -> R_N -> E -> G V (column-major)
   double* GG = RN + qq;            // G (column-major) -> U, W
-  float* G32 = reinterpret_cast<float*>(GG + qq);   // q x q floats each, column-major
+  float* G32 = reinterpret_cast<float*>(GG + qq);   // q x q floats each, column-major (later an FP64 q x q)
   float* V32 = G32 + qq;
   double* VD = GG + 2 * qq;        // the FP64 basis V (column-major)
   double* red = VD + qq;           // blockDim doubles
-  double* dg = red + bd;           // 2q doubles
+  double* dg = red + bd;           // q doubles
   __shared__ int bad;
   __shared__ int order[TTC_MAXQ];
   __shared__ double scl[2];   // powers of two that scale Psi and N to unit size
@@ -320,8 +321,9 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
     RP[i] = Psi[i] * scl[0];
     RN[i] = N[i] * scl[1];
   }
-  blk_chol2_upper_psd(RN, RP, q, dg);
+  blk_chol2_upper_psd(RN, RP, q);
   // G = R_N R_P^T, column-major: G[i][j] = sum_{t >= max(i, j)} R_N[i][t] R_P[j][t]
+  double fro = 0.0;
   for (int idx = tid; idx < qq; idx += bd) {
     const int j = idx / q, i = idx - j * q;
     double acc = 0.0;
@@ -329,31 +331,36 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
     GG[idx] = acc;
     G32[idx] = (float)acc;
     V32[idx] = (i == j) ? 1.f : 0.f;
+    fro = fma(acc, acc, fro);
   }
-  int sweeps = blk_hestenes<float>(G32, V32, q, 1e-6f, 24);
+  fro = blk_sum(fro, red);   // ||G||_F^2: columns below 1e-14 of it (FP32) are zero
+  int sweeps = blk_hestenes<float>(G32, V32, q, 1e-6f, (float)(1e-14 * fro), 24);
   const bool fp64 = P.bond_fp64 != 0;
+  // the basis in FP64 (converted once: conversions are FP64-pipe work)
+  for (int idx = tid; idx < qq; idx += bd) VD[idx] = (double)V32[idx];
   if (fp64) {
-    // V = V32 made orthonormal in FP64, V (I - E/2 + 3 E^2 / 8) with
-    // E = V32^T V32 - I (error O(|E|^3)); then FP64 sweeps on G V
+    // V made orthonormal in FP64, V (I - E/2 + 3 E^2 / 8) with
+    // E = V^T V - I (error O(|E|^3)); then FP64 sweeps on G V
     __syncthreads();
     for (int idx = tid; idx < qq; idx += bd) {     // E (R_N is not needed any more)
       const int j = idx / q, i = idx - j * q;
       double acc = (i == j) ? -1.0 : 0.0;
-      for (int t = 0; t < q; ++t) acc = fma((double)V32[i * q + t], (double)V32[j * q + t], acc);
+      for (int t = 0; t < q; ++t) acc = fma(VD[i * q + t], VD[j * q + t], acc);
       RN[idx] = acc;
     }
     __syncthreads();
-    for (int idx = tid; idx < qq; idx += bd) {     // F = I - E/2 + 3/8 E^2 (into VD)
+    double* F = reinterpret_cast<double*>(G32);     // G32 and V32 are not needed any more
+    for (int idx = tid; idx < qq; idx += bd) {     // F = I - E/2 + 3/8 E^2
       const int j = idx / q, i = idx - j * q;
       double acc = 0.0;
       for (int t = 0; t < q; ++t) acc = fma(RN[t * q + i], RN[j * q + t], acc);
-      VD[idx] = fma(0.375, acc, ((i == j) ? 1.0 : 0.0) - 0.5 * RN[idx]);
+      F[idx] = fma(0.375, acc, ((i == j) ? 1.0 : 0.0) - 0.5 * RN[idx]);
     }
     __syncthreads();
-    for (int idx = tid; idx < qq; idx += bd) {     // V32 F (into RN: E is not needed any more)
+    for (int idx = tid; idx < qq; idx += bd) {     // V F (into RN: E is not needed any more)
       const int j = idx / q, i = idx - j * q;
       double acc = 0.0;
-      for (int t = 0; t < q; ++t) acc = fma((double)V32[t * q + i], VD[j * q + t], acc);
+      for (int t = 0; t < q; ++t) acc = fma(VD[t * q + i], F[j * q + t], acc);
       RN[idx] = acc;
     }
     __syncthreads();
@@ -365,7 +372,7 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
       for (int t = 0; t < q; ++t) acc = fma(GG[t * q + i], VD[j * q + t], acc);
       RN[idx] = acc;
     }
-    sweeps += blk_hestenes<double>(RN, VD, q, 1e-14, 8);
+    sweeps += blk_hestenes<double>(RN, VD, q, 1e-14, 1e-30 * fro, 8);
   }
   __syncthreads();
   // squared singular values (column norms), NaN ordered last
@@ -392,7 +399,7 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
     const int a = idx / r, c = idx - (idx / r) * r;
     const int col = order[c];
     double acc = 0.0;
-    for (int t = 0; t <= a; ++t) acc = fma(RP[t * q + a], fp64 ? VD[col * q + t] : (double)V32[col * q + t], acc);
+    for (int t = 0; t <= a; ++t) acc = fma(RP[t * q + a], VD[col * q + t], acc);
     U[idx] = acc;
   }
   __syncthreads();
@@ -497,47 +504,93 @@ __device__ void slice_map(const DevProb& P, int k, int x, double* Y) {
   }
 }
 
-// Sums the nb block partials of a job into P.small[dst] in a fixed order:
-// G = blockDim / outputs thread groups split the partials, each thread keeps
-// four independent register accumulators (loads pipeline, FP64 adds overlap),
-// and the groups are combined in group order through shared memory.
-__device__ void finish_job(const DevProb& P, const Job& J, double* sm) {
-  const int d2 = J.rows * J.cols;
-  const int groups = max(1, min((int)blockDim.x / max(d2, 1), 32));
-  const double* src = P.red + J.red;
-  for (int base = 0; base < d2; base += blockDim.x / groups) {
+// Sums n partial rows of d values (src + row * d) into dst[0..d) in a fixed
+// order: G = blockDim / d thread groups split the rows, each thread keeps
+// four independent register accumulators (loads pipeline, FP64 adds
+// overlap), and the groups are combined in group order through shared
+// memory.  With `check`, a non-finite total flags the step.
+__device__ void sum_rows(const DevProb& P, const double* src, int n, int d, double* dst, double* sm, bool check) {
+  const int groups = max(1, min((int)blockDim.x / max(d, 1), 32));
+  for (int base = 0; base < d; base += blockDim.x / groups) {
     const int per = blockDim.x / groups;
     const int g = threadIdx.x / per, i = base + (threadIdx.x - g * per);
     double v = 0.0;
-    if (g < groups && i < d2) {
+    if (g < groups && i < d) {
       double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
       int bb = g;
-      for (; bb + 3 * groups < J.nb; bb += 4 * groups) {
-        a0 += __ldcg(src + (long long)bb * d2 + i);
-        a1 += __ldcg(src + (long long)(bb + groups) * d2 + i);
-        a2 += __ldcg(src + (long long)(bb + 2 * groups) * d2 + i);
-        a3 += __ldcg(src + (long long)(bb + 3 * groups) * d2 + i);
+      for (; bb + 3 * groups < n; bb += 4 * groups) {
+        a0 += __ldcg(src + (long long)bb * d + i);
+        a1 += __ldcg(src + (long long)(bb + groups) * d + i);
+        a2 += __ldcg(src + (long long)(bb + 2 * groups) * d + i);
+        a3 += __ldcg(src + (long long)(bb + 3 * groups) * d + i);
       }
-      for (; bb < J.nb; bb += groups) a0 += __ldcg(src + (long long)bb * d2 + i);
+      for (; bb < n; bb += groups) a0 += __ldcg(src + (long long)bb * d + i);
       v = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
     if (g < groups) sm[threadIdx.x] = v;
     __syncthreads();
-    if (g == 0 && i < d2) {
+    if (g == 0 && i < d) {
       double tot = 0.0;
       for (int gg = 0; gg < groups; ++gg) tot += sm[gg * per + threadIdx.x];
-      P.small[J.dst + i] = tot;
-      if (!isfinite(tot)) atomicOr(P.flags, 1u);   // an overflowed iterate ends the step as non-finite
+      dst[i] = tot;
+      if (check && !isfinite(tot)) atomicOr(P.flags, 1u);   // an overflowed iterate ends the step as non-finite
     }
     __syncthreads();
   }
 }
 
+// Reduction blocks per group of the stage reduction's first level, and the
+// group counters a stage may use (jobs of at most 1024 blocks each).
+constexpr int kGroup = 16;
+constexpr int kGroupCounters = (TTC_MAXM + 4) * (1024 / kGroup);
+__host__ __device__ inline int job_groups(int nb) { return (nb + kGroup - 1) / kGroup; }
+
+// The reduction of a stage after reduction block b of job j has written its
+// partial: the last block of each group of kGroup consecutive blocks sums
+// the group's partials in block order into a group partial, and the last
+// group of the stage sums every job's group partials in group order into
+// P.small (a fixed tree, so results are reproducible), resets the counters
+// and returns true; every other block returns false.  Spreading the sums
+// over the group finishers keeps the stage's last block from adding all
+// block partials alone on one SM.
+__device__ bool stage_reduce(const DevProb& P, const Stage& S, int j, int b, double* sm) {
+  __shared__ int last;
+  const Job& J = S.job[j];
+  const int dd = J.rows * J.cols;
+  const int g = b / kGroup, g0 = g * kGroup, gn = min(kGroup, J.nb - g0);
+  int gidx = g, total = 0;
+  for (int t = 0; t < S.njob; ++t) {
+    if (t < j) gidx += job_groups(S.job[t].nb);
+    total += job_groups(S.job[t].nb);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(P.gctr + gidx, 1) == gn - 1);
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  sum_rows(P, P.red + J.red + (long long)g0 * dd, gn, dd, P.red2 + J.red2 + (long long)g * dd, sm, false);
+  if (threadIdx.x == 0) P.gctr[gidx] = 0;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(P.counters + S.counter, 1) == total - 1);
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  for (int t = 0; t < S.njob; ++t) {
+    const Job& Jt = S.job[t];
+    sum_rows(P, P.red2 + Jt.red2, job_groups(Jt.nb), Jt.rows * Jt.cols, P.small + Jt.dst, sm, true);
+  }
+  if (threadIdx.x == 0) P.counters[S.counter] = 0;
+  __threadfence_block();
+  __syncthreads();
+  return true;
+}
+
 // ---- the stage kernel --------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_stage(const DevProb P, const Stage S) {
   extern __shared__ __align__(16) double sm[];
-  __shared__ int am_last;
   int b = blockIdx.x;
   for (int i = 0; i < S.nmap; ++i) {     // slice maps first
     const int k = S.map_k[i];
@@ -561,22 +614,7 @@ __global__ void __launch_bounds__(kThreads) k_stage(const DevProb P, const Stage
   for (int x = b; x < P.n[J.k]; x += J.nb) slice_contrib(P, S, J, x, acc, Y);
   double* out = P.red + J.red + (long long)b * dd;
   for (int i = threadIdx.x; i < dd; i += blockDim.x) out[i] = acc[i];
-  // the last reduction block finishes the stage
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int total = 0;
-    for (int t = 0; t < S.njob; ++t) total += S.job[t].nb;
-    int prev = atomicAdd(P.counters + S.counter, 1);
-    am_last = (prev == total - 1);
-  }
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  for (int t = 0; t < S.njob; ++t) finish_job(P, S.job[t], sm);
-  if (threadIdx.x == 0) P.counters[S.counter] = 0;
-  __threadfence_block();
-  __syncthreads();
+  if (!stage_reduce(P, S, j, b, sm)) return;   // the stage's last group finisher continues
   if (S.post == POST_SMALL_PROJ) {
     post_small_proj(P, sm);
   } else if (S.post == POST_BOND) {
@@ -597,7 +635,6 @@ __global__ void __launch_bounds__(kThreads) k_stage(const DevProb P, const Stage
 // warp order, so results stay reproducible.
 
 constexpr int kWarpsW = kThreads / 32;
-constexpr int kWScr = 3 * 16 * 16;   // doubles of scratch per warp at most (q = 16)
 
 // a warp's scratch: three q_max x q_max matrices of the problem (so blocks of
 // small problems take little shared memory and more of them stay resident)
@@ -758,7 +795,6 @@ __device__ void warp_slice_map(const DevProb& P, int k, int x, double* scr) {
 template <int NO>
 __device__ __forceinline__ void stage_w_body(const DevProb& P, const Stage& S, int b) {
   extern __shared__ __align__(16) double sm[];
-  __shared__ int am_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* scr = sm + warp * 3 * wscr_mat(P);
   for (int i = 0; i < S.nmap; ++i) {     // slice maps first, one slice per warp
@@ -816,22 +852,7 @@ __device__ __forceinline__ void stage_w_body(const DevProb& P, const Stage& S, i
     for (int w = 0; w < kWarpsW; ++w) t += sm[w * dd + o];
     out[o] = t;
   }
-  // the last reduction block finishes the stage
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int total = 0;
-    for (int t = 0; t < S.njob; ++t) total += S.job[t].nb;
-    int prev = atomicAdd(P.counters + S.counter, 1);
-    am_last = (prev == total - 1);
-  }
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  for (int t = 0; t < S.njob; ++t) finish_job(P, S.job[t], sm);
-  if (threadIdx.x == 0) P.counters[S.counter] = 0;
-  __threadfence_block();
-  __syncthreads();
+  if (!stage_reduce(P, S, j, b, sm)) return;   // the stage's last group finisher continues
   if (S.post == POST_SMALL_PROJ) {
     post_small_proj(P, sm);
   } else if (S.post == POST_BOND) {
@@ -1459,7 +1480,7 @@ int ttc_alloc_dense(ttc_ctx* c) {
     for (int k = 0; k <= m; ++k) qm = std::max(qm, P.q[k]);
     pl.warp = qm <= 16;
   }
-  long long red = 0;
+  long long red = 0, red2 = 0;
   int ctr = 1;   // counter 0 belongs to the slice reduction of the sampled pass
   bool warp_jobs = pl.warp;   // the metric stages below always use the block kernel
   auto mk = [&](int op, int k, int rows, int cols, int dst) {
@@ -1470,8 +1491,10 @@ int ttc_alloc_dense(ttc_ctx* c) {
     J.rows = rows;
     J.cols = cols;
     J.red = red;
+    J.red2 = red2;
     J.dst = dst;
     red += (long long)J.nb * rows * cols;
+    red2 += (long long)job_groups(J.nb) * rows * cols;
     return J;
   };
   auto blank = [&]() {
@@ -1532,6 +1555,17 @@ int ttc_alloc_dense(ttc_ctx* c) {
   TTC_TRY(ttc_alloc(c, (void**)&redp, sizeof(double) * (size_t)std::max(red + metric_extra, 1LL), false));
   P.red = redp;
   P.red_metric = red;
+  // group partials: the plan's jobs, then the metric stages' extra jobs
+  long long metric_extra2 = 0;
+  for (int k = 0; k < m; ++k) metric_extra2 += 2LL * job_groups(nblocks_for((int)c->n[k])) * TTC_MAXR * TTC_MAXR;
+  double* red2p = nullptr;
+  TTC_TRY(ttc_alloc(c, (void**)&red2p, sizeof(double) * (size_t)std::max(red2 + metric_extra2, 1LL), false));
+  P.red2 = red2p;
+  P.red2_metric = red2;
+  int* gctr = nullptr;   // group counters, reused by every stage (a stage resets the ones it used)
+  TTC_TRY(ttc_alloc(c, (void**)&gctr, sizeof(int) * kGroupCounters, false));
+  TTC_CUDA(cudaMemsetAsync(gctr, 0, sizeof(int) * kGroupCounters, c->stream));
+  P.gctr = gctr;
   TTC_TRY(ttc_alloc(c, (void**)&pl.metric_part, sizeof(double) * 2 * 1024, false));
 
   int qmax = 1, rmax = 1;
@@ -1777,7 +1811,7 @@ int ttc_launch_metric(ttc_ctx* c, int which) {
   const int m = P.m;
   for (int k = 0; k < m; ++k) {
     Stage S = pl.metric[which][k];
-    long long red = P.red_metric;
+    long long red = P.red_metric, red2 = P.red2_metric;
     const int ra = P.r[k + 1];
     const int sb = which == 0 ? P.rt[k + 1] : P.r[k + 1];
     Job J = S.job[0];
@@ -1785,13 +1819,16 @@ int ttc_launch_metric(ttc_ctx* c, int which) {
     J.rows = ra;
     J.cols = sb;
     J.red = red;
+    J.red2 = red2;
     J.dst = P.off_mlam[1][k + 1];
     red += (long long)J.nb * ra * sb;
+    red2 += (long long)job_groups(J.nb) * ra * sb;
     S.job[S.njob++] = J;
     J.op = OP_DBB;
     J.rows = sb;
     J.cols = sb;
     J.red = red;
+    J.red2 = red2;
     J.dst = P.off_mlam[2][k + 1];
     S.job[S.njob++] = J;
     TTC_TRY(launch_stage(c, S, pl.smem_stage));

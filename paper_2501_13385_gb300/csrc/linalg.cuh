@@ -264,14 +264,15 @@ static __device__ void blk_chol_linv64(const double* G, int ldg, int n, double* 
 
 // Upper Cholesky factors of two symmetric positive semidefinite n x n
 // matrices (row-major, n <= 64) at once, in place: A = R_A^T R_A and
-// B = R_B^T R_B.  Right-looking, one pivot per barrier: the Schur complement
-// is updated whole (both triangles), so the update of pivot j reads column j
-// below the diagonal while row j is scaled into the factor.  A pivot at or
-// below 1e-14 of the largest diagonal entry is rounding noise of a
-// numerically singular Gram (its square root would turn noise of 1e-16 into
-// rows of size 1e-8): it gives a zero row, which keeps R^T R equal to the
-// matrix on its numerical range.  diag: 2n doubles.
-static __device__ void blk_chol2_upper_psd(double* A, double* B, int n, double* diag) {
+// B = R_B^T R_B.  Right-looking, two barriers per pivot: row j of the factor
+// (the Schur complement's row j over its pivot's square root), then the
+// update of the upper triangle of the trailing block by that row's outer
+// product.  A pivot at or below 1e-14 of the largest diagonal entry is
+// rounding noise of a numerically singular Gram (its square root would turn
+// noise of 1e-16 into rows of size 1e-8): it gives a zero row, which keeps
+// R^T R equal to the matrix on its numerical range.  The strict lower
+// triangles are zeroed.
+static __device__ void blk_chol2_upper_psd(double* A, double* B, int n) {
   const int tid = threadIdx.x, bd = blockDim.x;
   __syncthreads();
   double ma = 0.0, mb = 0.0;
@@ -284,34 +285,30 @@ static __device__ void blk_chol2_upper_psd(double* A, double* B, int n, double* 
     const double da = A[j * n + j], db = B[j * n + j];
     const double ra = (da > ta) ? rsqrt(da) : 0.0;
     const double rb = (db > tb) ? rsqrt(db) : 0.0;
-    const int t = n - 1 - j;
-    for (int idx = tid; idx < 2 * t * t; idx += bd) {
-      const bool second = idx >= t * t;
-      const int e = second ? idx - t * t : idx;
-      const int i = j + 1 + e / t, c = j + 1 + (e - (e / t) * t);
-      double* M = second ? B : A;
-      const double rr = second ? rb : ra;
-      M[i * n + c] = fma(-(M[i * n + j] * rr), M[c * n + j] * rr, M[i * n + c]);
-    }
+    const int t = n - j;   // row j from the diagonal on
     for (int idx = tid; idx < 2 * t; idx += bd) {
       const bool second = idx >= t;
-      const int c = j + 1 + (second ? idx - t : idx);
+      const int c = j + (second ? idx - t : idx);
       double* M = second ? B : A;
-      M[j * n + c] *= second ? rb : ra;
+      const double rr = second ? rb : ra;
+      M[j * n + c] = (c == j) ? (second ? db : da) * rr : M[j * n + c] * rr;
     }
-    if (tid == 0) {
-      diag[j] = da * ra;        // sqrt(da), or 0
-      diag[n + j] = db * rb;
+    __syncthreads();
+    const int u = n - 1 - j;   // trailing block, upper triangle by rows
+    for (int idx = tid; idx < 2 * u * u; idx += bd) {
+      const bool second = idx >= u * u;
+      const int e = second ? idx - u * u : idx;
+      const int i = j + 1 + e / u, c = j + 1 + (e - (e / u) * u);
+      if (c < i) continue;
+      double* M = second ? B : A;
+      M[i * n + c] = fma(-M[j * n + i], M[j * n + c], M[i * n + c]);
     }
     __syncthreads();
   }
   for (int idx = tid; idx < 2 * n * n; idx += bd) {
     const bool second = idx >= n * n;
     const int e = second ? idx - n * n : idx;
-    const int i = e / n, c = e - (e / n) * n;
-    double* M = second ? B : A;
-    if (c < i) M[e] = 0.0;
-    else if (c == i) M[e] = diag[(second ? n : 0) + i];
+    if (e % n < e / n) (second ? B : A)[e] = 0.0;
   }
   __syncthreads();
 }
@@ -329,12 +326,14 @@ static __device__ void blk_chol2_upper_psd(double* A, double* B, int n, double* 
 //   t = sgn(z) / (|z| + sqrt(1 + z^2)),  z = (b - a) / (2c),
 //   g_p <- cs g_p - sn g_q,  g_q <- sn g_p + cs g_q,  cs = 1/sqrt(1 + t^2), sn = t cs.
 // The sums of a pair are butterfly reductions over its lanes, identical on
-// every lane, so the lanes agree on the rotation.  Stops after a sweep
-// without rotations or after max_sweeps; returns the sweeps run.  The
+// every lane, so the lanes agree on the rotation.  Columns whose squared
+// norm is at or below `floor` are zero to the working precision and are not
+// rotated (their directions are noise and never settle).  Stops after a
+// sweep without rotations or after max_sweeps; returns the sweeps run.  The
 // rotations act on the factor, not on its Gram, so singular values of very
 // different sizes keep their relative accuracy.
 template <typename T>
-static __device__ int blk_hestenes(T* G, T* V, int n, T tol, int max_sweeps) {
+static __device__ int blk_hestenes(T* G, T* V, int n, T tol, T floor, int max_sweeps) {
   const int lp = n <= 16 ? 4 : 8;
   const int lane = threadIdx.x & 31;
   const int slot = (threadIdx.x >> 5) * (32 / lp) + lane / lp;
@@ -360,31 +359,40 @@ static __device__ int blk_hestenes(T* G, T* V, int n, T tol, int max_sweeps) {
           q = max(pa, pb);
           act = q < n;   // not the dummy column of an odd n
         }
+        constexpr int MR = 8;   // rows per lane: n <= 16 with lp = 4, n <= 64 with lp = 8
+        T ca[MR], cb[MR];
         T al = T(0), be = T(0), ga = T(0);
-        if (act)
-          for (int row = sub; row < n; row += lp) {
-            const T a = G[p * n + row], b = G[q * n + row];
-            al = fma(a, a, al);
-            be = fma(b, b, be);
-            ga = fma(a, b, ga);
-          }
+#pragma unroll
+        for (int h = 0; h < MR; ++h) {
+          const int row = sub + h * lp;
+          ca[h] = (act && row < n) ? G[p * n + row] : T(0);
+          cb[h] = (act && row < n) ? G[q * n + row] : T(0);
+          al = fma(ca[h], ca[h], al);
+          be = fma(cb[h], cb[h], be);
+          ga = fma(ca[h], cb[h], ga);
+        }
         for (int o = lp / 2; o > 0; o >>= 1) {
           al += __shfl_xor_sync(0xffffffffu, al, o);
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (act && fabs(ga) > tol * sqrt(al * be)) {
+        // a column below the floor is zero to the working precision: its
+        // direction is noise and never settles, so it is not rotated
+        if (act && fmin(al, be) > floor && fabs(ga) > tol * sqrt(al * be)) {
           const T z = (be - al) / (T(2) * ga);
           const T az = fabs(z);
           const T tt = az > T(1e15) ? T(0.5) / z : copysign(T(1), z) / (az + sqrt(fma(z, z, T(1))));
           const T cs = rsqrt(fma(tt, tt, T(1))), sn = cs * tt;
-          for (int row = sub; row < n; row += lp) {
-            const T a = G[p * n + row], b = G[q * n + row];
-            G[p * n + row] = fma(cs, a, -sn * b);
-            G[q * n + row] = fma(sn, a, cs * b);
-            const T x = V[p * n + row], y = V[q * n + row];
-            V[p * n + row] = fma(cs, x, -sn * y);
-            V[q * n + row] = fma(sn, x, cs * y);
+#pragma unroll
+          for (int h = 0; h < MR; ++h) {
+            const int row = sub + h * lp;
+            if (row < n) {
+              G[p * n + row] = fma(cs, ca[h], -sn * cb[h]);
+              G[q * n + row] = fma(sn, ca[h], cs * cb[h]);
+              const T x = V[p * n + row], y = V[q * n + row];
+              V[p * n + row] = fma(cs, x, -sn * y);
+              V[q * n + row] = fma(sn, x, cs * y);
+            }
           }
           if (sub == 0) rotated = 1;
         }

@@ -179,7 +179,7 @@ __global__ void k_eval(const DevProb P, const int32_t* __restrict__ idx, long lo
 // the pass kernel for (precision, rank bucket R, register size RC)
 int launch_pass_kernel(bool f32, int R, int RC, const PassLaunch& L) {
   if (R <= 8) return f32 ? ttc_pass_small_f32(RC, L) : ttc_pass_small_f64(RC, L);
-  return ttc_pass_large(f32, R, L);
+  return ttc_pass_large(f32, R, R == 16 ? 16 : (RC <= 24 ? 24 : 32), L);
 }
 
 template <typename T, int R>
@@ -205,11 +205,8 @@ int launch_pass(ttc_ctx* c, int RC) {
   const int nsegb = ttc_seg_blocks(P);
   k_segment_reduce<T><<<nsegb, kSegThreads, 0, c->stream>>>(P, nsegb);
   TTC_CUDA(cudaGetLastError());
-  int passes = 1;
-  if (R <= 8) {   // one launch per non-empty mode class
-    passes = 0;
-    for (int cls = 0; cls < 3; ++cls) passes += ttc_pass_class_blocks(P, cls) > 0 ? 1 : 0;
-  }
+  int passes = 0;   // one launch per non-empty mode class
+  for (int cls = 0; cls < 3; ++cls) passes += ttc_pass_class_blocks(P, cls) > 0 ? 1 : 0;
   c->nlaunch += 1 + passes;
   return TTC_OK;
 }

@@ -11,8 +11,8 @@
 //
 // Layout: entries of mode k are stored in mode-k order, so a slice x is a
 // contiguous segment; segments are cut into chunks of TTC_CHUNK entries, each
-// reduced by one warp (small ranks) or one block (large ranks) without
-// atomics; a second kernel sums the chunk partials of each slice in chunk
+// reduced by one warp (small ranks, and the first and last modes at any rank)
+// or one block (interior modes at large ranks) without atomics; a second kernel sums the chunk partials of each slice in chunk
 // order in FP64.  Core slices are read from padded mirrors (row stride R =
 // rank bucket, 16-byte aligned) with 16-byte loads; the pass's own slice is
 // constant on a chunk and sits in shared memory.
@@ -669,93 +669,124 @@ __device__ __forceinline__ void sample_project_warp(const DevProb& P, const int 
     warp_chunk_general<T, R, RC, KIND>(P, k, beg, end, Ts, out);
 }
 
-// Large ranks (R >= 16): one block reduces one chunk.  The rank-one terms of
-// 256 entries at a time are staged in shared memory and every thread owns a
-// tile of the r_k x r_{k+1} output.
-template <typename T, int R>
-__device__ __forceinline__ void sample_project_block(const DevProb& P, const int blk) {
+// Large ranks (R >= 16), interior modes: one block reduces one chunk.  Each
+// thread forms one entry's interfaces (one gathered row each, or chains of
+// core slices), its value and its residual; the value is one dot product
+// with a table row when a table covers exactly modes <= k (a prefix row,
+// times r) or modes >= k (l times a suffix row), else l^T T_k(x) r.  The
+// block stages g*l and r of NE entries in shared memory and thread t
+// accumulates OPT = R*R/256 outputs of the r_{k-1} x r_k partial over them:
+// column t mod R, rows OPT*(t div R) ... (threads whose rows or column lie
+// beyond the ranks skip the accumulation).
+template <typename T, int R, int RC>
+__device__ __forceinline__ void sample_project_interior(const DevProb& P, const int call) {
+  constexpr int NE = TTC_NT;            // entries staged per round
+  constexpr int RS = (RC + 3) & ~3;     // staged row length (16-byte multiple)
+  constexpr int OPT = (R * R) / TTC_NT; // outputs per thread
+  static_assert(OPT >= 1 && OPT * TTC_NT == R * R && RS % OPT == 0, "output tiling");
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* Ts = reinterpret_cast<T*>(smraw);   // R*R: the pass's own slice
-  T* Lg = Ts + R * R;                     // [TTC_NT][R]
-  T* Rv = Lg + TTC_NT * R;                // [TTC_NT][R]
-
-  int k = 0;
-  while (k + 1 < P.m && blk >= P.chunk_base[k + 1]) ++k;
-  const int c = blk - P.chunk_base[k];
+  T* Ts = reinterpret_cast<T*>(smraw);  // R*R: the pass's own slice
+  T* Lg = Ts + R * R;                    // [NE][RS]: g * l
+  T* Rv = Lg + NE * RS;                  // [NE][RS]: r
+  int k = 1;
+  while (k + 2 < P.m && call >= P.chunk_base[k + 1]) ++k;
+  const int c = call - P.chunk_base[k];
   const int x = P.cseg[k][c];
   const int beg = P.seg[k][x] + (c - P.cfirst[k][x]) * TTC_CHUNK;
   const int end = min(beg + TTC_CHUNK, P.seg[k][x + 1]);
   const int ra = P.r[k], rb = P.r[k + 1];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   {
     const T* S = core_ptr<T>(P, k) + (long long)x * R * R;
     for (int i = tid; i < R * R; i += TTC_NT) {
-      int a = i / R, b = i - (i / R) * R;
+      const int a = i / R, b = i - (i / R) * R;
       Ts[i] = (a < ra && b < rb) ? S[pad_idx(P, k, a, b)] : T(0);
     }
   }
   __syncthreads();
   T* out = reinterpret_cast<T*>(P.part) + (long long)(P.chunk_base[k] + c) * P.part_stride;
-  // output tiles: R == 16 -> one element per thread, R == 32 -> 2 x 2
-  constexpr int TA = (R == 32) ? 2 : 1;
-  constexpr int TB = (R == 32) ? 2 : 1;
-  const int a0 = (tid / (R / TB)) * TA, b0 = (tid % (R / TB)) * TB;
-  T acc[TA][TB];
-#pragma unroll
-  for (int i = 0; i < TA; ++i)
-#pragma unroll
-    for (int j = 0; j < TB; ++j) acc[i][j] = 0;
-  T s2 = 0;
-  for (int it = 0; it < kEPT; ++it) {
-    const int e = beg + it * TTC_NT + tid;
-    T lv[R], rv[R];
-    T g = 0;
-    if (e < end) {
-      const Code words = load_code(P, k, e);
-      T v = interfaces<T, R, R>(P, k, words, Ts, lv, rv);
-      g = v - yval<T>(P, k, e);
-      if (P.keep_residual && k == 0) P.g[P.perm[0][e]] = (double)g;
-    } else {
-      zero(lv);
-      zero(rv);
-    }
-    s2 = fma(g, g, s2);
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < R; ++a) {
-      Lg[tid * R + a] = g * lv[a];
-      Rv[tid * R + a] = rv[a];
-    }
-    __syncthreads();
-    const int cnt = min(TTC_NT, max(0, end - (beg + it * TTC_NT)));
-    for (int t = 0; t < cnt; ++t) {
-      T la[TA], rbv[TB];
-#pragma unroll
-      for (int i = 0; i < TA; ++i) la[i] = Lg[t * R + a0 + i];
-#pragma unroll
-      for (int j = 0; j < TB; ++j) rbv[j] = Rv[t * R + b0 + j];
-#pragma unroll
-      for (int i = 0; i < TA; ++i)
-#pragma unroll
-        for (int j = 0; j < TB; ++j) acc[i][j] = fma(la[i], rbv[j], acc[i][j]);
+  RowSrc<T> ls{}, rs{}, vs{};
+  const bool rows = left_src<T>(P, k, ls) && right_src<T>(P, k, rs);
+  int vmode = 0;   // 0: l^T T_k(x) r, 1: prefix row . r, 2: l . suffix row
+  {
+    const int tp = P.pre_tab[k + 1], tq = P.suf_tab[k - 1];
+    if (tp >= 0 && P.tab_j[tp] == k + 1) {
+      vs = {tab_ptr<T>(P) + P.tab_row0[tp] * P.R, P.tab_word[tp], P.tab_shift[tp], (1u << P.tab_bits[tp]) - 1u, P.R};
+      vmode = 1;
+    } else if (tq >= 0 && P.tab_j[tq] == k) {
+      vs = {tab_ptr<T>(P) + P.tab_row0[tq] * P.R, P.tab_word[tq], P.tab_shift[tq], (1u << P.tab_bits[tq]) - 1u, P.R};
+      vmode = 2;
     }
   }
-  T v = warp_sum(s2);
+  const uint32_t* __restrict__ code = P.code[k];
+  const T* __restrict__ yk = y_ptr<T>(P, k);
+  const uint64_t pol_stream = policy_evict_first(), pol_rows = policy_evict_last();
+  const int ob = tid % R, oa0 = (tid / R) * OPT;
+  const bool owner = oa0 < ra && ob < rb;
+  T acc[OPT];
+#pragma unroll
+  for (int u = 0; u < OPT; ++u) acc[u] = 0;
+  T s2 = 0;
+  for (int base = beg; base < end; base += NE) {
+    const int e = base + tid;
+    T lv[RC], rv[RC];
+    zero(lv);
+    zero(rv);
+    T g = 0;
+    if (e < end) {
+      const Code w = load_code_at(code, P.W, e, pol_stream);
+      const T yv = ld_stream(yk + e, pol_stream);
+      T v = 0;
+      if (rows) {
+        load_row_hint<RC>(row_of(ls, w), RC, lv, pol_rows);
+        load_row_hint<RC>(row_of(rs, w), RC, rv, pol_rows);
+        if (vmode != 0) {
+          T vr[RC];
+          zero(vr);
+          load_row_hint<RC>(row_of(vs, w), RC, vr, pol_rows);
+#pragma unroll
+          for (int a = 0; a < RC; ++a) v = fma(vr[a], vmode == 1 ? rv[a] : lv[a], v);
+        } else {
+          v = slice_value<T, R, RC>(Ts, ra, rb, lv, rv);
+        }
+      } else {
+        v = interfaces<T, R, RC>(P, k, w, Ts, lv, rv);
+      }
+      g = v - yv;
+    }
+    s2 = fma(g, g, s2);
+    __syncthreads();   // the previous round's staged rows are consumed
+#pragma unroll
+    for (int a = 0; a < RS; ++a) {
+      Lg[tid * RS + a] = a < RC ? g * lv[a] : T(0);
+      Rv[tid * RS + a] = a < RC ? rv[a] : T(0);
+    }
+    __syncthreads();
+    const int cnt = min(NE, end - base);
+    if (owner) {
+      for (int i = 0; i < cnt; ++i) {
+        const T rvb = Rv[i * RS + ob];
+        const T* lrow = Lg + i * RS + oa0;
+#pragma unroll
+        for (int u = 0; u < OPT; ++u) acc[u] = fma(lrow[u], rvb, acc[u]);
+      }
+    }
+  }
+  // block sum of g^2 in warp order (the staged area is free again)
+  s2 = warp_sum(s2);
   __syncthreads();
-  if (lane == 0) Lg[warp] = v;
+  if ((tid & 31) == 0) Lg[tid >> 5] = s2;
   __syncthreads();
   if (tid == 0) {
     T tot = 0;
-    for (int w = 0; w < TTC_NT / 32; ++w) tot += Lg[w];
+    for (int wi = 0; wi < TTC_NT / 32; ++wi) tot += Lg[wi];
     out[0] = tot;
   }
+  if (owner) {
 #pragma unroll
-  for (int i = 0; i < TA; ++i)
-#pragma unroll
-    for (int j = 0; j < TB; ++j) {
-      const int a = a0 + i, b = b0 + j;
-      if (a < ra && b < rb) out[1 + a * rb + b] = acc[i][j];
-    }
+    for (int u = 0; u < OPT; ++u)
+      if (oa0 + u < ra) out[1 + (oa0 + u) * rb + ob] = acc[u];
+  }
 }
 
 // chunks [c0, c1) of a mode class (small ranks; see ttc_pass_class_range)
@@ -772,11 +803,14 @@ __device__ __forceinline__ void class_range(const DevProb& P, int mc, int& c0, i
   }
 }
 
-// MC: a mode class (small ranks, one chunk per warp) or PC_ALL (large ranks,
-// one chunk per block over all modes)
+// MC: a mode class.  The first and last modes (and every mode at small
+// ranks) reduce one chunk per warp; the interior modes at large ranks
+// (R >= 16) one chunk per block.
 template <typename T, int R, int RC, int MC>
 __device__ __forceinline__ void sample_project(const DevProb& P, const int blk) {
-  if constexpr (MC != PC_ALL) {
+  if constexpr (MC == PC_MIDDLE && R >= 16) {
+    sample_project_interior<T, R, RC>(P, P.chunk_base[1] + blk);
+  } else {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int warp = threadIdx.x >> 5;
     int c0, c1;
@@ -784,8 +818,6 @@ __device__ __forceinline__ void sample_project(const DevProb& P, const int blk) 
     const int call = c0 + blk * kWarps + warp;
     if (call >= c1) return;
     sample_project_warp<T, R, RC, MC>(P, call, reinterpret_cast<T*>(smraw) + warp * R * R);
-  } else {
-    sample_project_block<T, R>(P, blk);
   }
 }
 
@@ -794,7 +826,9 @@ __device__ __forceinline__ void sample_project(const DevProb& P, const int blk) 
 // small FP32 interior ranks two (16 warps, two gathers in flight each)
 template <typename T, int RC, int MC>
 constexpr int min_blocks() {
-  return sizeof(T) != 4 ? 1 : (MC == PC_FIRST || MC == PC_LAST) ? (RC <= 6 ? 4 : 3) : (MC == PC_MIDDLE && RC <= 5) ? 2 : 1;
+  return sizeof(T) != 4 || RC > 8 ? 1
+         : (MC == PC_FIRST || MC == PC_LAST) ? (RC <= 6 ? 4 : 3)
+         : (MC == PC_MIDDLE && RC <= 5) ? 2 : 1;
 }
 
 template <typename T, int R, int RC, int MC>
@@ -831,10 +865,12 @@ __global__ void __launch_bounds__(TTC_NT, (min_blocks<T, RC, MC>())) k_sample_pr
   sample_project<T, R, RC, MC>(Ps, blockIdx.x - __ldg(base + p));
 }
 
-template <typename T>
-inline size_t pass_smem(int R) {
-  if (R <= 8) return sizeof(T) * (size_t)(kWarps * R * R);
-  return sizeof(T) * (size_t)(R * R + 2 * TTC_NT * R);
+// per mode class: a slice per warp, or (interior modes, R >= 16) the slice
+// and the staged rows of the block
+template <typename T, int R, int RC>
+inline size_t pass_smem_class(int mc) {
+  if (R >= 16 && mc == PC_MIDDLE) return sizeof(T) * (size_t)(R * R + 2 * TTC_NT * ((RC + 3) & ~3));
+  return sizeof(T) * (size_t)(kWarps * R * R);
 }
 
 // the pass of a single problem (g == nullptr) or a batch group: small ranks
@@ -842,8 +878,9 @@ inline size_t pass_smem(int R) {
 // launch over all chunks
 template <typename T, int R, int RC>
 int launch(const PassLaunch& L) {
-  const size_t smem = pass_smem<T>(R);
-  if constexpr (R <= 8) {
+  const size_t sm0 = pass_smem_class<T, R, RC>(PC_FIRST), sm1 = pass_smem_class<T, R, RC>(PC_MIDDLE),
+               sm2 = pass_smem_class<T, R, RC>(PC_LAST);
+  {
     // the interior class on the issuing stream, the first and last classes
     // on the fork's streams (when given), joined back before returning
     cudaStream_t sf = L.st, sl = L.st;
@@ -856,20 +893,20 @@ int launch(const PassLaunch& L) {
     }
     if (L.g) {
       if (L.g->pass_blocks_c[PC_FIRST] > 0)
-        k_sample_project_batch<T, R, RC, PC_FIRST><<<L.g->pass_blocks_c[PC_FIRST], TTC_NT, smem, sf>>>(
+        k_sample_project_batch<T, R, RC, PC_FIRST><<<L.g->pass_blocks_c[PC_FIRST], TTC_NT, sm0, sf>>>(
             L.g->probs, L.g->pass_base_c[PC_FIRST], L.g->nprob);
       if (L.g->pass_blocks_c[PC_MIDDLE] > 0)
-        k_sample_project_batch<T, R, RC, PC_MIDDLE><<<L.g->pass_blocks_c[PC_MIDDLE], TTC_NT, smem, L.st>>>(
+        k_sample_project_batch<T, R, RC, PC_MIDDLE><<<L.g->pass_blocks_c[PC_MIDDLE], TTC_NT, sm1, L.st>>>(
             L.g->probs, L.g->pass_base_c[PC_MIDDLE], L.g->nprob);
       if (L.g->pass_blocks_c[PC_LAST] > 0)
-        k_sample_project_batch<T, R, RC, PC_LAST><<<L.g->pass_blocks_c[PC_LAST], TTC_NT, smem, sl>>>(
+        k_sample_project_batch<T, R, RC, PC_LAST><<<L.g->pass_blocks_c[PC_LAST], TTC_NT, sm2, sl>>>(
             L.g->probs, L.g->pass_base_c[PC_LAST], L.g->nprob);
     } else {
       const int b0 = ttc_pass_class_blocks(*L.P, PC_FIRST), b1 = ttc_pass_class_blocks(*L.P, PC_MIDDLE),
                 b2 = ttc_pass_class_blocks(*L.P, PC_LAST);
-      if (b0 > 0) k_sample_project<T, R, RC, PC_FIRST><<<b0, TTC_NT, smem, sf>>>(*L.P);
-      if (b1 > 0) k_sample_project<T, R, RC, PC_MIDDLE><<<b1, TTC_NT, smem, L.st>>>(*L.P);
-      if (b2 > 0) k_sample_project<T, R, RC, PC_LAST><<<b2, TTC_NT, smem, sl>>>(*L.P);
+      if (b0 > 0) k_sample_project<T, R, RC, PC_FIRST><<<b0, TTC_NT, sm0, sf>>>(*L.P);
+      if (b1 > 0) k_sample_project<T, R, RC, PC_MIDDLE><<<b1, TTC_NT, sm1, L.st>>>(*L.P);
+      if (b2 > 0) k_sample_project<T, R, RC, PC_LAST><<<b2, TTC_NT, sm2, sl>>>(*L.P);
     }
     TTC_CUDA(cudaGetLastError());
     if (L.fork) {
@@ -878,26 +915,25 @@ int launch(const PassLaunch& L) {
       TTC_CUDA(cudaStreamWaitEvent(L.st, L.fork->join[0], 0));
       TTC_CUDA(cudaStreamWaitEvent(L.st, L.fork->join[1], 0));
     }
-  } else {
-    if (L.g)
-      k_sample_project_batch<T, R, RC, PC_ALL><<<L.g->pass_blocks, TTC_NT, smem, L.st>>>(L.g->probs, L.g->pass_base,
-                                                                                          L.g->nprob);
-    else
-      k_sample_project<T, R, RC, PC_ALL><<<ttc_pass_blocks(*L.P, R), TTC_NT, smem, L.st>>>(*L.P);
   }
-  TTC_CUDA(cudaGetLastError());
   return TTC_OK;
 }
 
+template <typename T, int R, int RC, int MC>
+int opt_in_class(size_t smem) {
+  if (smem > 48 * 1024) {
+    TTC_CUDA(cudaFuncSetAttribute(k_sample_project<T, R, RC, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    TTC_CUDA(cudaFuncSetAttribute(k_sample_project_batch<T, R, RC, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  }
+  return TTC_OK;
+}
 template <typename T, int R, int RC>
 int opt_in() {
-  const size_t smem = pass_smem<T>(R);
-  if (smem > 48 * 1024) {
-    TTC_CUDA(cudaFuncSetAttribute(k_sample_project<T, R, RC, PC_ALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-    TTC_CUDA(cudaFuncSetAttribute(k_sample_project_batch<T, R, RC, PC_ALL>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  }
+  TTC_TRY((opt_in_class<T, R, RC, PC_FIRST>(pass_smem_class<T, R, RC>(PC_FIRST))));
+  TTC_TRY((opt_in_class<T, R, RC, PC_MIDDLE>(pass_smem_class<T, R, RC>(PC_MIDDLE))));
+  TTC_TRY((opt_in_class<T, R, RC, PC_LAST>(pass_smem_class<T, R, RC>(PC_LAST))));
   return TTC_OK;
 }
 

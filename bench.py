@@ -1,21 +1,32 @@
 #!/usr/bin/env python
 """Benchmark of the PRGD hot path on one GB300.
 
-Workload: the orthogonal-cubic tensor-completion problem, order 3, 200 per
-mode, TT-ranks (1,5,5,1), 5% of entries observed (|Omega| = 400 000),
-noiseless; synthetic, seeded.  A step is one PRGD iteration (sampled pass over
-Omega, weights, weighted tangent projection, rank-2r assembly, TT-rounding
-retraction) in the MIXED mode (FP32 sampled pass, FP64 dense stages) of a
-batch of B independent such problems (default 32, seeds differ), launched as
-one CUDA graph, with all inputs resident in device memory.  The batch's
-inputs are larger than L2; for small batches L2 is flushed (256 MB write)
-between timed steps, outside the timed brackets.
+Headline workload: the hyperspectral-shaped completion problem (the
+paper's hyperspectral-image experiment, Section 5, with a synthetic tensor
+in place of the image data set, which is not available): 256 x 256 x 128,
+sum of 20 separable smooth terms plus N(0, 1e-3^2) noise, TT-ranks
+(1,20,20,1), 10% of the entries observed (|Omega| = 838 861).  A step is one
+PRGD iteration (sampled pass over Omega, weights, weighted tangent
+projection, the steepest step of Eq. (PRGD stepsize), rank-2r assembly,
+TT-rounding retraction) in the MIXED mode (FP32 sampled pass, FP64 dense
+stages) of a batch of B independent such problems (seeds differ), launched
+as one CUDA graph, all inputs resident in device memory.  The batch's inputs
+are larger than L2.
 
-Prints ONE JSON line.  `--impl reference` times the FP64 CPU oracle on the
-same workload instead (the reference arm; rank 0 only).
+The step size: the constant form of Theorem 4.1 at the tuned scale 1.5
+diverges on this workload and converges ~10x slower at 0.5 (oracle runs);
+the steepest step converges, so it is this workload's policy.
 
-Multi-GPU: one process per GPU (torchrun), each solving its own replica
-(seed = rank); value = entries of all ranks / max-over-ranks time.
+Prints ONE JSON line with the headline figures plus, under `configs`, the
+other workloads (the planted order-4 problem, the orthogonal cubic problem,
+the tomography-shaped problem), each with its batched throughput, iterations
+and time to rel.err <= 1e-6 (mixed precision against plain FP64 on the
+GPU) and its error against the FP64 CPU oracle.  `--impl reference` times
+the FP64 CPU oracle on the headline workload instead (the reference arm;
+rank 0 only).
+
+Multi-GPU: one process per GPU (torchrun), each solving its own replicas
+(disjoint seeds); value = entries of all ranks / max-over-ranks time.
 """
 from __future__ import annotations
 
@@ -32,26 +43,36 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Ω-entries/s & PRGD iters/s to rel.err≤1e-6 vs FP64 GPU; p50/p99 solve ms"
-WORKLOAD = {"workload": "orthogonal_cubic", "d": 3, "n": 200, "ranks": [1, 5, 5, 1], "omega": 400000,
-            "frac": 0.05, "noise": 0.0}
+HEADLINE = {"workload": "hyperspectral_like", "shape": [256, 256, 128], "ranks": [1, 20, 20, 1],
+            "omega": 838861, "frac": 0.10, "noise_std": 1e-3, "terms": 20, "step_rule": "steepest"}
+GOLDEN = os.path.join(ROOT, "tests", "golden", "full_size_solutions.json")
+L2_BYTES = 129 * 2 ** 20
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ttc", choices=["ttc", "reference"])
+    ap.add_argument("--batch", type=int, default=8, help="headline problems per step (one CUDA graph launch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-solves", type=int, default=3)
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads")
+    ap.add_argument("--e2e-solves", type=int, default=2)
     ap.add_argument("--e2e-iters", type=int, default=20)
-    ap.add_argument("--serve-requests", type=int, default=64,
-                    help="requests streamed through the serving engine (0: skip)")
-    ap.add_argument("--serve-mixed", type=int, default=32,
+    ap.add_argument("--serve-mixed", type=int, default=512,
                     help="requests of the mixed serving stream (0: skip)")
-    ap.add_argument("--batch", type=int, default=32,
-                    help="independent problems per step (one CUDA graph launch); 1 = a single problem")
+    ap.add_argument("--serve-max-entries", type=int, default=1_000_000)
+    ap.add_argument("--serve-slots", type=int, default=32)
     return ap.parse_args()
+
+
+_T0 = time.perf_counter()
+
+
+def phase(msg):
+    """Progress of the run on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
 
 
 def dist_env():
@@ -62,34 +83,28 @@ def dist_env():
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle timing (reference arm and cpu_baseline); runs in a fresh process
-# with one BLAS/OpenMP thread so `cores` is what it actually used.
+# CPU oracle timing (reference arm and cpu_baseline); every process runs one
+# problem single-threaded, so `cores` is what the run actually used.
 # ---------------------------------------------------------------------------
 ORACLE_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, %(root)r)
 import oracle as o
 from paper_2501_13385_gb300 import workloads as w
-P = w.orthogonal_cubic(%(seed)d)
+P = w.hyperspectral_like(%(seed)d)
 cur = P.init
 times = []
 t_end = time.perf_counter() + %(budget)f
 for i in range(%(warm)d + %(steps)d):
     t0 = time.perf_counter()
-    cur, _ = o.prgd_step(cur, P.idx, P.y, P.n, P.r, eps_rel=1.0, alpha_scale=1.5)
+    cur, _ = o.prgd_step(cur, P.idx, P.y, P.n, P.r, eps_rel=1.0, alpha_scale=1.5, step="adaptive")
     dt = time.perf_counter() - t0
     if i >= %(warm)d:
         times.append(dt)
-    if %(bounded)d and i >= %(warm)d + 2 and time.perf_counter() > t_end:
+    if i >= %(warm)d and time.perf_counter() > t_end:
         break
 print(json.dumps({"N": P.N, "times": times}))
 """
-
-
-def _oracle_cmd(seed, warm, steps, budget_s, bounded):
-    code = ORACLE_SNIPPET % {"root": ROOT, "seed": seed, "warm": warm, "steps": steps, "budget": budget_s,
-                             "bounded": 1 if bounded else 0}
-    return [sys.executable, "-c", code]
 
 
 def _one_thread_env():
@@ -97,12 +112,6 @@ def _one_thread_env():
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
         env[v] = "1"
     return env
-
-
-def run_oracle(seed, warm, steps, budget_s, bounded):
-    out = subprocess.run(_oracle_cmd(seed, warm, steps, budget_s, bounded), env=_one_thread_env(),
-                         capture_output=True, text=True, check=True)
-    return json.loads(out.stdout.strip().splitlines()[-1])
 
 
 def host_cores():
@@ -113,13 +122,16 @@ def host_cores():
 
 
 def run_oracle_parallel(procs, warm, steps, budget_s):
-    """The oracle on `procs` independent problems at once (one single-threaded
-    process per host core, seeds 0..procs-1), each bounded to about budget_s
-    of work; returns (entries processed per second over the wall time, the
-    per-process results).  Processes are started by fork+exec."""
+    """The oracle on `procs` independent headline problems at once (one
+    single-threaded process per host core, seeds 0..procs-1), each stopping
+    after the first timed step past budget_s; returns (Omega-entries per
+    second of all processes, per-process results, wall seconds)."""
     t0 = time.perf_counter()
-    ps = [subprocess.Popen(_oracle_cmd(i, warm, steps, budget_s, True), env=_one_thread_env(),
-                           stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True) for i in range(procs)]
+    ps = []
+    for i in range(procs):
+        code = ORACLE_SNIPPET % {"root": ROOT, "seed": i, "warm": warm, "steps": steps, "budget": budget_s}
+        ps.append(subprocess.Popen([sys.executable, "-c", code], env=_one_thread_env(), stdout=subprocess.PIPE,
+                                   stderr=subprocess.PIPE, text=True))
     res = []
     for p in ps:
         out, err = p.communicate()
@@ -127,33 +139,27 @@ def run_oracle_parallel(procs, warm, steps, budget_s):
             raise RuntimeError(f"oracle process failed: {err[-400:]}")
         res.append(json.loads(out.strip().splitlines()[-1]))
     wall = time.perf_counter() - t0
-    timed = sum(sum(r["times"]) for r in res)
-    work = sum(r["N"] * len(r["times"]) for r in res)
-    # rate over the timed steps of all processes, which overlapped: entries / (timed seconds per process)
-    rate = work / (timed / procs)
-    return rate, res, wall
+    per_proc = [r["N"] * len(r["times"]) / sum(r["times"]) for r in res]
+    return sum(per_proc), res, wall
 
 
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    # one oracle process per host core, each on its own problem of the
-    # workload (the batch's problems are independent), bounded in time
     cores = host_cores()
-    steps = max(1, min(args.steps, 20))
-    value, res, wall = run_oracle_parallel(cores, min(args.warmup, 1), steps, budget_s=60.0)
+    value, res, wall = run_oracle_parallel(cores, 0, max(1, min(args.steps, 3)), budget_s=45.0)
     t = [x for r in res for x in r["times"]]
     ms = 1e3 * statistics.mean(t)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Ω-entries/s", "n_gpus": args.gpus,
-        "steps": min(len(r["times"]) for r in res), "warmup": min(args.warmup, 1), "ms_per_step": ms,
+        "steps": min(len(r["times"]) for r in res), "warmup": 0, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(WORKLOAD, precision="fp64", batch=cores, parallelism=f"{cores} host processes (CPU)"),
+        "config": dict(HEADLINE, precision="fp64", batch=cores, parallelism=f"{cores} host processes (CPU)"),
         "iters_per_s": cores * 1e3 / ms,
         "cpu_baseline": {"value": value, "unit": "Ω-entries/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{cores} problems in parallel, one per core, {len(t)} PRGD iterations in "
-                                   f"total ({wall:.0f} s wall)"},
+                         "sample": f"{cores} headline problems in parallel, one single-threaded oracle process "
+                                   f"per core, {len(t)} PRGD iterations in total ({wall:.0f} s wall)"},
         "e2e": {"value": value, "unit": "Ω-entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -211,6 +217,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ---------------------------------------------------------------------------
+# algorithmic work of the sampled pass (the per-unit figures of the roofline)
+# ---------------------------------------------------------------------------
 def code_plan(n):
     """Packed-code layout of the coordinates (fields never straddle a 32-bit
     word): per mode (word, shift, bits), and the words per entry."""
@@ -225,14 +234,13 @@ def code_plan(n):
     return plan, (4 if W == 3 else W)
 
 
-def table_rows(P, cap_rows):
+def table_rows(P):
     """Valid rows of the interface tables the library keeps (prefix tables
     over modes 0..j-1, j >= 2, and suffix tables over modes j..d-1, j <= d-2,
     whose modes share one code word and whose bit-indexed row count stays
-    within the cap)."""
-    import math
+    within min(2^17, max(4096, 4|Omega|)))."""
     plan, _ = code_plan(P.n)
-    cap = min(1 << 17, max(4096, 4 * P.N)) if cap_rows is None else cap_rows
+    cap = min(1 << 17, max(4096, 4 * P.N))
     rows, m = [], P.m
 
     def ok(first, last):
@@ -251,42 +259,46 @@ def table_rows(P, cap_rows):
     return rows
 
 
-def algorithmic_bytes_per_launch(P, chunk=1024):
-    """Bytes the sampled pass must move per launch for one problem: for every
+def rank_bucket(P):
+    rmax = max(P.r)
+    return 4 if rmax <= 4 else 8 if rmax <= 8 else 16 if rmax <= 16 else 32
+
+
+def pass_bytes(P, chunk=1024):
+    """Bytes the sampled pass must move per step for one problem: for every
     mode k, every entry's packed code (4W bytes) and FP32 value (4 bytes), one
-    FP32 partial (1 + r_k r_{k+1} values) written per chunk of `chunk` entries
-    of a slice, and, read once, the valid rows of the interface tables and the
-    padded FP32 core slices (rows of R = rank-bucket floats)."""
+    FP32 partial (1 + r_k r_{k+1} values) per chunk of `chunk` entries of a
+    slice, and, read once, the valid rows of the interface tables (r values
+    each) and the core slices (r_k r_{k+1} values each)."""
     import numpy as np
     _, W = code_plan(P.n)
-    rmax = max(P.r)
-    R = 4 if rmax <= 4 else 8 if rmax <= 8 else 16 if rmax <= 16 else 32
     total = 0
     for k in range(P.m):
         counts = np.bincount(P.idx[:, k], minlength=P.n[k])
         chunks = int(np.sum((counts + chunk - 1) // chunk))
         total += P.N * (4 * W + 4) + chunks * (1 + P.r[k] * P.r[k + 1]) * 4
-        total += P.n[k] * R * R * 4
-    total += sum(table_rows(P, None)) * R * 4
+        total += P.n[k] * P.r[k] * P.r[k + 1] * 4
+    rows = table_rows(P)
+    total += sum(rows) * max(P.r) * 4
     return total
 
 
-def load_traffic(kernel_file, batch):
-    """dram bytes per launch of the dominant kernel from the committed ncu
-    summary, if it was taken on the current kernel source and batch size."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        rec = json.load(open(path))
-        src = open(kernel_file, "rb").read()
-        if (rec.get("source_sha1") == hashlib.sha1(src).hexdigest() and rec.get("workload") == WORKLOAD["workload"]
-                and rec.get("batch") == batch):
-            return rec.get("dram_bytes_per_launch")
-    except Exception:
-        pass
-    return None
+def pass_flops(P):
+    """FP32 FMAs the sampled pass must do per step for one problem when every
+    interface is one table or core row (the case of the headline workload):
+    per entry and mode k, the value l^T T_k(x) r (r_{k-1} r_k + min(r_{k-1},
+    r_k) FMAs) and the rank-one update g l r^T (r_{k-1} r_k FMAs); as FLOPs
+    (2 per FMA)."""
+    fma = 0
+    for k in range(P.m):
+        a, b = P.r[k], P.r[k + 1]
+        fma += P.N * (a * b + min(a, b) + a * b)
+    return 2 * fma
 
 
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
 def ttc_arm(args):
     rank, world, local = dist_env()
     if world > 1:
@@ -295,6 +307,7 @@ def ttc_arm(args):
     import torch
     import torch.distributed as dist
 
+    import oracle as o
     from paper_2501_13385_gb300 import build, ttc
     from paper_2501_13385_gb300 import workloads as w
     from paper_2501_13385_gb300.replicas import max_over_ranks, replica_seeds, whole_job_rate
@@ -304,10 +317,9 @@ def ttc_arm(args):
     build.build()
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream(dev)
+    tstream = torch.cuda.Stream(dev)
+    sp = tstream.cuda_stream
     B = max(1, args.batch)
-    probs = [w.orthogonal_cubic(s) for s in replica_seeds(rank, B)]
-    N = probs[0].N
 
     def make_ctx(P, prec, stop=ttc.STOP_NONE, **kw):
         c = ttc.Context(P.n, P.r, precision=prec, stop_rule=stop, **kw)
@@ -315,100 +327,192 @@ def ttc_arm(args):
         c.set_cores(P.init)
         return c
 
-    ctxs = [make_ctx(P, ttc.PREC_MIXED) for P in probs]
-    batch = ttc.Batch(ctxs, stream=stream.cuda_stream)
-    flush = None
-    l2_note = "inputs larger than L2 (no flush)"
-    if B * algorithmic_bytes_per_launch(probs[0]) < 4 * 129 * 2 ** 20:
-        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-        l2_note = "flushed between timed steps (256 MB write)"
-
-    for _ in range(args.warmup):
-        batch.step()
-    batch.sync()
-    batch.profile_enable(True)
-    batch.step()                          # recaptures with the timing event nodes
-    batch.sync()
-    batch.profile_read(reset=True)
-
-    K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    launches0 = batch.launch_count()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(K):
-            ev[i][0].record(stream)
+    def time_batch(probs, steps, warmup, prec=ttc.PREC_MIXED, clocks=False, **kw):
+        """K timed batched steps on `tstream`, L2 flushed between steps when
+        the batch's inputs fit in L2; returns a dict of figures."""
+        ctxs = [make_ctx(P, prec, **kw) for P in probs]
+        batch = ttc.Batch(ctxs, stream=sp)
+        flush = None
+        note = "inputs larger than L2 (no flush)"
+        if sum(pass_bytes(P) for P in probs) < 4 * L2_BYTES:
+            flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+            note = "flushed between timed steps (256 MB write)"
+        for _ in range(warmup):
             batch.step()
-            ev[i][1].record(stream)
-            if flush is not None:
-                flush.zero_()
+        batch.sync()
+        batch.profile_enable(True)
+        batch.step()                          # recaptures with the timing event nodes
+        batch.sync()
+        batch.profile_read(reset=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        launches0 = batch.launch_count()
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    launches = batch.launch_count() - launches0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    kern_ms, kern_n = batch.profile_read(reset=True)
-    batch.close()
-    for c in ctxs:
-        c.close()
-    total_ms = max_over_ranks(total_ms, world)
+        clk = ClockSampler(local) if clocks else None
+        if clk:
+            clk.__enter__()
+        with torch.cuda.stream(tstream):
+            for i in range(steps):
+                ev[i][0].record(tstream)
+                batch.step()
+                ev[i][1].record(tstream)
+                if flush is not None:
+                    flush.zero_()
+        torch.cuda.synchronize()
+        if clk:
+            clk.__exit__()
+        if world > 1:
+            dist.barrier()
+        launches = batch.launch_count() - launches0
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        kern_ms, kern_n = batch.profile_read(reset=True)
+        batch.close()
+        for c in ctxs:
+            c.close()
+        return {"step_ms": step_ms, "total_ms": sum(step_ms), "launches": launches,
+                "pass_ms": kern_ms / max(kern_n, 1), "pass_launches": kern_n, "l2": note,
+                "clocks": clk.summary() if clk else None}
+
+    def timed_solve(P, prec, stop, tol, max_iter, truth=None, **kw):
+        """A solve from P.init through the C ABI, timed end to end on the
+        host (graphs captured by an untimed first run)."""
+        with make_ctx(P, prec, stop, tol=tol, max_iter=max_iter, **kw) as c:
+            if truth is not None:
+                c.set_truth(truth)
+            c.solve()
+            c.set_cores(P.init)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = c.solve()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            return res, 1e3 * dt, c.get_cores()
+
+    def to_tol(P, step_kw, noisy):
+        """Iterations and time to rel.err <= 1e-6 against the FP64 GPU
+        solution: for noiseless data that solution is T* itself (checked
+        to 1e-10 by the parity tests); for noisy data it is the FP64 GPU
+        solve under the stop rule of the paper's noise experiment (Section 5,
+        step change <= 1e-5 max(1, ||T||)), the answer the plain FP64 GPU
+        PRGD gives."""
+        out = {}
+        if noisy:
+            res, ms, ref = timed_solve(P, ttc.PREC_FP64, ttc.STOP_STEP, 1e-5, 2000, **step_kw)
+            out["fp64_reference"] = {"rule": "step change <= 1e-5 max(1, ||T||)", "iters": res["iters"],
+                                     "converged": res["converged"], "ms": ms}
+        else:
+            ref = P.truth
+        for name, prec in (("mixed", ttc.PREC_MIXED), ("fp64", ttc.PREC_FP64)):
+            res, ms, _ = timed_solve(P, prec, ttc.STOP_RELERR, 1e-6, 2000, truth=ref, **step_kw)
+            out[name] = {"iters": res["iters"], "converged": res["converged"], "ms": ms,
+                         "polish_iter": res["polish_iter"]}
+        return out
+
+    def error_vs_golden(name, P, step_kw):
+        """The MIXED solve under Section 5's stop rule against the oracle's
+        solution under the same rule (tests/golden/full_size_solutions.json):
+        relative distance estimated on the stored sample entries."""
+        gold = json.load(open(GOLDEN))[name]
+        with make_ctx(P, ttc.PREC_MIXED, ttc.STOP_STEP, tol=gold["tol"], max_iter=1000, **step_kw) as c:
+            res = c.solve()
+            vals = c.eval(np.asarray(gold["idx"], dtype=np.int32))
+        ref = gold["iterates"].get(str(res["iters"]))
+        out = {"rule": "step change <= 1e-5 max(1, ||T||) (Section 5)", "iters": res["iters"],
+               "oracle_iters": gold["stop"], "polish_iter": res["polish_iter"]}
+        if ref is not None:
+            rv = np.asarray(ref["values"])
+            out["rel_dist_sampled"] = float(np.sqrt(np.sum((vals - rv) ** 2) / np.sum(rv ** 2)))
+        return out
+
+    def error_vs_live_oracle(P, step_kw, oracle_kw):
+        """The MIXED solve to rel.err <= 1e-6 (vs T*) against the oracle's
+        FP64 solve of the same problem to 1e-12: relative Frobenius distance."""
+        with make_ctx(P, ttc.PREC_MIXED, ttc.STOP_RELERR, tol=1e-6, max_iter=500, **step_kw) as c:
+            c.set_truth(P.truth)
+            res = c.solve()
+            got = c.get_cores()
+        ref = o.solve(P.init, P.idx, P.y, P.n, P.r, truth=P.truth, eps_rel=1.0, alpha_scale=1.5, max_iter=300,
+                      tol=1e-12, **oracle_kw).cores
+        return {"rule": "rel.err vs T* <= 1e-6", "iters": res["iters"],
+                "rel_dist": o.tt_dist(got, ref) / o.tt_norm(ref)}
+
+    steep = {"step_rule": ttc.STEP_STEEPEST}
+
+    # ---- the headline: batched MIXED steps of the hyperspectral-shaped workload
+    phase("generating the headline workload")
+    probs = [w.hyperspectral_like(s) for s in replica_seeds(rank, B)]
+    phase("timing the headline batch")
+    N = probs[0].N
+    K = args.steps
+    hb = time_batch(probs, K, args.warmup, clocks=True, **steep)
+    total_ms = max_over_ranks(hb["total_ms"], world)
     ms_per_step = total_ms / K
     value = whole_job_rate(world, B, N, K, total_ms)
 
-    # iterations and time to rel.err <= 1e-6 (vs T*) for one problem, mixed and plain FP64
-    P = probs[0]
-    to_tol = {}
-    # (the steepest step and RGD -- uniform metric with the steepest step -- are
-    # the paper's comparison points, Section 5)
-    runs = (("mixed", ttc.PREC_MIXED, {}), ("fp64", ttc.PREC_FP64, {}),
-            ("steepest_mixed", ttc.PREC_MIXED, {"step_rule": ttc.STEP_STEEPEST}),
-            ("rgd_steepest_mixed", ttc.PREC_MIXED, {"step_rule": ttc.STEP_STEEPEST, "metric": ttc.METRIC_UNIFORM}))
-    for name, prec, var in runs:
-        with make_ctx(P, prec, ttc.STOP_RELERR, tol=1e-6, max_iter=200, **var) as c2:
-            c2.set_truth(P.truth)
-            res = c2.solve()
-        iters = res["iters"]
-        with make_ctx(P, prec, ttc.STOP_NONE, max_iter=iters, **var) as c3:
-            c3.solve()                     # capture the graphs
-            c3.set_cores(P.init)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            c3.solve()
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-        to_tol[name] = {"iters": iters, "converged": res["converged"], "ms": 1e3 * dt,
-                        "polish_iter": res["polish_iter"]}
+    # roofline of the sampled pass (bracketed by events inside the graph)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    clock_mhz = (hb["clocks"] or {}).get("sm_max_mhz") or 2070.0
+    fp32_peak = 152 * 128 * 2 * clock_mhz * 1e6 / 1e12      # FP32 SIMT: 152 SMs x 128 FMA lanes x 2
+    flops = sum(pass_flops(P) for P in probs)
+    achieved = flops / (hb["pass_ms"] / 1e3) / 1e12
+    alg_bytes = sum(pass_bytes(P) for P in probs)
+    hbm_peak = peaks.get("hbm_gbs")
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": None,
+            "kernel": "k_sample_project_batch<float,32,24,{first,interior,last}> (three mode-class launches, "
+                      "concurrent)", "kernel_ms": hb["pass_ms"],
+            "launches_timed": hb["pass_launches"], "algorithmic_flops_per_launch": flops,
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "hbm_gbs_at_algorithmic_bytes": alg_bytes / (hb["pass_ms"] / 1e3) / 1e9,
+            "hbm_peak": hbm_peak, "hbm_peak_source": "measured" if hbm_peak else "fallback",
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock",
+            "step_share": hb["pass_ms"] / ms_per_step}
 
-    # the tomography-shaped workload of Section 5 (order 10, mode 4, ranks 4,
-    # 80 000 entries): iterations and time to rel.err <= 1e-6, mixed precision
-    Q = w.qst_like(rank)
-    with make_ctx(Q, ttc.PREC_MIXED, ttc.STOP_RELERR, tol=1e-6, max_iter=200) as c2:
-        c2.set_truth(Q.truth)
-        qres = c2.solve()
-    with make_ctx(Q, ttc.PREC_MIXED, ttc.STOP_NONE, max_iter=qres["iters"]) as c3:
-        c3.solve()
-        c3.set_cores(Q.init)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        c3.solve()
-        torch.cuda.synchronize()
-        qdt = time.perf_counter() - t0
-    qst = {"workload": "qst_like", "qubits": 10, "ranks": 4, "omega": Q.N, "iters": qres["iters"],
-           "converged": qres["converged"], "ms": 1e3 * qdt}
+    # ---- per-result errors and time to tolerance of the headline workload
+    phase("headline: time to tolerance and error against the oracle")
+    P0 = probs[0]
+    head_tol = to_tol(P0, steep, noisy=True)
+    head_err = error_vs_golden("hyperspectral_like", P0, steep)
 
-    # end to end through the public API from pinned host buffers: every step
-    # copies all B problems' observations and starting cores in, runs
-    # e2e_iters batched iterations and reads all cores back
+    # ---- the other workloads
+    configs = {}
+    if not args.no_configs:
+        specs = [
+            ("planted_small", w.planted_small, 32, {}, {}, False),
+            ("orthogonal_cubic", w.orthogonal_cubic, 32, {}, {}, False),
+            ("tomography_like", w.tomography_like, 8, {}, {}, True),
+        ]
+        for name, maker, bsz, kw, okw, noisy in specs:
+            phase(f"workload {name}")
+            cp = [maker(s) for s in replica_seeds(rank, bsz)]
+            tb = time_batch(cp, max(5, K // 2), 3, **kw)
+            cms = max_over_ranks(tb["total_ms"], world) / max(5, K // 2)
+            entry = {"batch": bsz, "omega": cp[0].N, "n": cp[0].n, "ranks": cp[0].r, "ms_per_step": cms,
+                     "value": whole_job_rate(world, bsz, cp[0].N, 1, cms), "unit": "Ω-entries/s",
+                     "pass_ms": tb["pass_ms"], "l2": tb["l2"],
+                     "to_rel_err_1e-6": to_tol(cp[0], kw, noisy)}
+            if noisy:
+                entry["error_vs_oracle"] = error_vs_golden(name, cp[0], kw)
+            else:
+                entry["error_vs_oracle"] = error_vs_live_oracle(cp[0], kw, okw)
+            configs[name] = entry
+
+    phase("end to end")
+    # ---- end to end through the public API from pinned host buffers: every
+    # step copies all B problems' observations and starting cores in, builds
+    # their layouts, runs e2e_iters batched iterations and reads the cores back
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     idx_h = [pin(P.idx.astype(np.int32)) for P in probs]
     y_h = [pin(P.y) for P in probs]
     init_h = [[pin(c) for c in P.init] for P in probs]
     e2e_ms = []
     out_bytes = 0
-    ectx = [ttc.Context(P.n, P.r, precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_NONE) for P in probs]
+    ectx = [ttc.Context(P.n, P.r, precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_NONE, **steep) for P in probs]
     for rep in range(args.e2e_solves + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -430,132 +534,107 @@ def ttc_arm(args):
     e2e_step_ms = max_over_ranks(statistics.mean(e2e_ms), world)
     e2e_val = whole_job_rate(world, B, N, args.e2e_iters, e2e_step_ms)
 
-    # serving: a burst of solve requests (rel.err <= 1e-6 against T*, mixed
-    # precision) through the continuous-batching engine with B slots
-    serving = None
-    if args.serve_requests > 0:
-        sprobs = [probs[i] if i < B else w.orthogonal_cubic(rank * 100000 + 50000 + i)
-                  for i in range(args.serve_requests)]
-        sopt = ttc.default_options(precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_RELERR, tol=1e-6, max_iter=200)
-        with ttc.Server(max_slots=B) as srv:
-            # one request first so that kernel set-up is outside the measurement
-            srv.poll(srv.submit(P.n, P.r, P.idx, P.y, P.init, truth=P.truth, options=sopt), cores=False)
-            s0 = srv.stats()
-            t0 = time.perf_counter()
-            tickets = [srv.submit(Q.n, Q.r, Q.idx, Q.y, Q.init, truth=Q.truth, options=sopt) for Q in sprobs]
-            res = [srv.poll(t) for t in tickets]
-            wall = time.perf_counter() - t0
-            s1 = srv.stats()
-        lat = sorted(r["latency_ms"] for r in res)
-        pct = lambda q: lat[min(len(lat) - 1, max(0, int(np.ceil(q * len(lat))) - 1))]
-        serving = {
-            "requests": len(res), "max_slots": B, "stop": "rel.err <= 1e-6 vs T*, mixed precision",
-            "converged": sum(1 for r in res if r["converged"]),
-            "requests_per_s": len(res) / wall, "wall_ms": 1e3 * wall,
-            "latency_p50_ms": pct(0.50), "latency_p99_ms": pct(0.99),
-            "mean_iters": float(np.mean([r["iters"] for r in res])),
-            "entry_iters_per_s": (s1["entry_iterations"] - s0["entry_iterations"]) / wall,
-            "gpu_launches": s1["launches"] - s0["launches"],
-        }
-
-    # the mixed serving stream (orders 3-12, modes 4-256, ranks 2-16, |Omega|
-    # log-uniform, capped at 2e5 here to keep the run short): a burst of all
-    # requests, then Poisson arrivals at 70% of the burst's request rate
+    # ---- the mixed serving stream
     mixed = None
     if args.serve_mixed > 0:
-        reqs = [w.random_request(1000 + i, max_entries=200_000) for i in range(args.serve_mixed)]
-        # a stream of unknown problems takes the steepest step: the constant
-        # step's tuned scale diverges on some high-order, low-oversampling draws
-        mopt = ttc.default_options(precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_RELERR, tol=1e-6, max_iter=500,
-                                   step_rule=ttc.STEP_STEEPEST)
-
-        def run_stream(gaps):
-            with ttc.Server(max_slots=B) as srv:
-                t0 = time.perf_counter()
-                tk = []
-                for Q, gap in zip(reqs, gaps):
-                    if gap > 0:
-                        time.sleep(gap)
-                    tk.append(srv.submit(Q.n, Q.r, Q.idx, Q.y, Q.init, truth=Q.truth, options=mopt))
-                rs = [srv.poll(t, cores=False) for t in tk]
-                wall_s = time.perf_counter() - t0
-                st = srv.stats()
-            lat = sorted(r["latency_ms"] for r in rs)
-            q = lambda f: lat[min(len(lat) - 1, max(0, int(np.ceil(f * len(lat))) - 1))]
-            return {"requests": len(rs), "wall_ms": 1e3 * wall_s, "requests_per_s": len(rs) / wall_s,
-                    "latency_p50_ms": q(0.5), "latency_p99_ms": q(0.99),
-                    "converged": sum(1 for r in rs if r["converged"]),
-                    "failed": sum(1 for r in rs if r["status"] not in ("TTC_OK", "TTC_ENOTCONV")),
-                    "mean_iters": float(np.mean([r["iters"] for r in rs])),
-                    "entry_iters_per_s": st["entry_iterations"] / wall_s}
-        burst = run_stream([0.0] * len(reqs))
-        prng = np.random.default_rng(7)
-        rate = 0.7 * burst["requests_per_s"]
-        poisson = run_stream(list(prng.exponential(1.0 / rate, len(reqs))))
-        poisson["arrival_rate_per_s"] = rate
-        mixed = {"workload": "random_request stream (orders 3-12, modes 4-256, ranks 2-16, |Omega| <= 2e5)",
-                 "stop": "rel.err <= 1e-6 vs T* or 500 iterations, mixed precision, steepest step",
-                 "max_slots": B,
-                 "burst": burst, "poisson_70pct": poisson}
-
-    # roofline of the dominant kernel: the batched sampled pass, one launch per step
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if peak else "fallback"
-    peak = peak or 6800.0
-    alg = sum(algorithmic_bytes_per_launch(P) for P in probs)
-    kern_avg_ms = kern_ms / max(kern_n, 1)
-    achieved = alg / (kern_avg_ms / 1e3) / 1e9
-    traffic = load_traffic(os.path.join(ROOT, "paper_2501_13385_gb300", "csrc", "omega_pass.cuh"), B)
-    rmax0 = max(probs[0].r)
-    R_bucket = 4 if rmax0 <= 4 else 8 if rmax0 <= 8 else 16 if rmax0 <= 16 else 32
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": f"k_sample_project_batch<float,{R_bucket},{max(probs[0].r)}>", "kernel_ms": kern_avg_ms,
-            "launches_timed": kern_n, "algorithmic_bytes_per_launch": alg, "peak_source": peak_src}
+        phase("serving stream")
+        mixed = serving_stream(args, rank, ttc, w, np)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = run_oracle(seed=0, warm=1, steps=100, budget_s=10.0, bounded=True)
-        t = r["times"]
-        one = r["N"] / statistics.mean(t)
+        phase("CPU baseline (oracle)")
         cores = host_cores()
-        allv, res, wall = run_oracle_parallel(cores, 1, 100, budget_s=10.0)
+        allv, res, wall = run_oracle_parallel(cores, 0, 2, budget_s=10.0)
         cpu = {"value": allv, "unit": "Ω-entries/s", "cores": cores, "kind": "oracle",
-               "sample": f"{cores} orthogonal_cubic problems at once, one single-threaded oracle process per "
-                         f"host core, ~10 s each ({sum(len(x['times']) for x in res)} PRGD iterations)",
-               "one_core": {"value": one, "cores": 1,
-                            "sample": f"{len(t)} PRGD iterations of one problem, ~10 s of one core"}}
+               "sample": f"{cores} headline problems at once (hyperspectral_like seeds 0..{cores - 1}), one "
+                         f"single-threaded oracle process per host core, steepest step, "
+                         f"{sum(len(x['times']) for x in res)} PRGD iterations in {wall:.0f} s"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Ω-entries/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 sampled pass + f64 dense stages", "data": "synthetic",
-            "config": dict(WORKLOAD, batch=B, precision="mixed", l2=l2_note,
+            "config": dict(HEADLINE, batch=B, precision="mixed", l2=hb["l2"],
                            parallelism="replicas" if world > 1 else "single GPU"),
             "iters_per_s": 1e3 / ms_per_step,
             "problem_iters_per_s": B * 1e3 / ms_per_step,
-            "step_ms_p50": statistics.median(step_ms), "step_ms_p99": sorted(step_ms)[max(0, int(0.99 * K) - 1)],
-            "to_rel_err_1e-6": to_tol,
-            "qst_to_rel_err_1e-6": qst,
+            "step_ms_p50": statistics.median(hb["step_ms"]),
+            "step_ms_p99": sorted(hb["step_ms"])[max(0, int(math.ceil(0.99 * K)) - 1)],
+            "to_rel_err_1e-6": head_tol,
+            "error_vs_oracle": head_err,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "Ω-entries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": out_bytes, "iters_per_step": args.e2e_iters,
                     "ms_per_step": e2e_step_ms},
-            "gpu_launches": launches,
-            "serving": serving,
+            "gpu_launches": hb["launches"],
+            "configs": configs,
             "serving_mixed_stream": mixed,
-            "clocks": clk.summary(),
+            "clocks": hb["clocks"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _request(args_tuple):
+    """One request of the mixed stream (built in a worker process)."""
+    seed, max_entries = args_tuple
+    from paper_2501_13385_gb300 import workloads as w
+    return w.random_request(seed, max_entries=max_entries)
+
+
+def serving_stream(args, rank, ttc, w, np):
+    """The mixed serving stream: orders 3-12, modes 4-256, interior ranks
+    2-16, |Omega| log-uniform in [1e3, max_entries], each request a seeded
+    Gaussian-core truth with uniform Omega, solved to rel.err <= 1e-6 vs T*
+    or 500 iterations with the steepest step (the safe step for unknown
+    problems: the constant step's tuned scale diverges on some of them); a
+    burst of all requests, then Poisson arrivals at 70% of the burst's
+    request rate.""" 
+    import multiprocessing as mp
+    n = args.serve_mixed
+    with mp.get_context("spawn").Pool(max(1, min(16, host_cores()))) as pool:
+        reqs = pool.map(_request, [(rank * 100000 + 1000 + i, args.serve_max_entries) for i in range(n)])
+    mopt = ttc.default_options(precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_RELERR, tol=1e-6, max_iter=500,
+                               step_rule=ttc.STEP_STEEPEST)
+
+    def run_stream(gaps):
+        with ttc.Server(max_slots=args.serve_slots) as srv:
+            t0 = time.perf_counter()
+            tk = []
+            for Q, gap in zip(reqs, gaps):
+                if gap > 0:
+                    time.sleep(gap)
+                tk.append(srv.submit(Q.n, Q.r, Q.idx, Q.y, Q.init, truth=Q.truth, options=mopt))
+            rs = [srv.poll(t, cores=False) for t in tk]
+            wall_s = time.perf_counter() - t0
+            st = srv.stats()
+        ok = sorted(r["latency_ms"] for r in rs if r["converged"])
+        q = lambda v, f: v[min(len(v) - 1, max(0, int(np.ceil(f * len(v))) - 1))] if v else None
+        return {"requests": len(rs), "wall_ms": 1e3 * wall_s, "requests_per_s": len(rs) / wall_s,
+                "latency_p50_ms": q(ok, 0.5), "latency_p99_ms": q(ok, 0.99),
+                "converged": len(ok),
+                "not_converged": sum(1 for r in rs if r["status"] == "TTC_ENOTCONV"),
+                "failed": sum(1 for r in rs if r["status"] not in ("TTC_OK", "TTC_ENOTCONV")),
+                "mean_iters": float(np.mean([r["iters"] for r in rs])),
+                "entry_iters_per_s": st["entry_iterations"] / wall_s, "gpu_launches": st["launches"]}
+    phase(f"serving: {len(reqs)} requests generated")
+    burst = run_stream([0.0] * len(reqs))
+    phase("serving: burst done")
+    prng = np.random.default_rng(7)
+    rate = 0.7 * burst["requests_per_s"]
+    poisson = run_stream(list(prng.exponential(1.0 / rate, len(reqs))))
+    poisson["arrival_rate_per_s"] = rate
+    sizes = sorted(Q.N for Q in reqs)
+    return {"workload": f"random_request stream (orders 3-12, modes 4-256, ranks 2-16, |Omega| log-uniform "
+                        f"1e3..{args.serve_max_entries:.0e})",
+            "omega_min": sizes[0], "omega_max": sizes[-1], "omega_median": sizes[len(sizes) // 2],
+            "stop": "rel.err <= 1e-6 vs T* or 500 iterations, mixed precision, steepest step",
+            "latency": "submission to completion; percentiles over converged requests",
+            "max_slots": args.serve_slots, "burst": burst, "poisson_70pct": poisson}
 
 
 def main():

@@ -338,8 +338,9 @@ void ttc_server_destroy(ttc_server* s);
  * and rb[d+1] (host, first and last 1, each <= 32), and host arrays of d
  * DEVICE pointers a_dev[k], b_dev[k] to cores in the host layout of this
  * header (ra[k] x n[k] x ra[k+1] row-major).  Every one of the d* = prod n_k
- * entries is evaluated in FP64, so d* is limited to 2^32; larger shapes return
- * TTC_EUNSUPPORTED.  Output: out_dev[0] = ||A - B||_F^2, out_dev[1] =
+ * entries is evaluated in FP64, so d* is limited to 2^32 and the work, d*
+ * times sum_k (ra[k] ra[k+1] + rb[k] rb[k+1]) FMAs, to 2^34; larger shapes
+ * return TTC_EUNSUPPORTED.  Output: out_dev[0] = ||A - B||_F^2, out_dev[1] =
  * ||B||_F^2 (two doubles of device memory), written on `cuda_stream` (NULL:
  * the default stream); the call returns without waiting.
  *
@@ -348,9 +349,11 @@ void ttc_server_destroy(ttc_server* s);
  * process exits; it is never cleared (each call writes the slots it reads).
  * All calls share it, so calls that overlap on the GPU (different streams or
  * host threads without ordering) race.  The first call on each device looks
- * up the array's device address with that device current; make that first
- * call before any stream capture.  Errors: TTC_EINVAL (null pointers, bad
- * ranks), TTC_EUNSUPPORTED (limits above), TTC_ECUDA (launch failure). */
+ * up the array's device address with that device current and keeps it for
+ * the life of the process; make that first call before any stream capture,
+ * and do not use the call after a cudaDeviceReset of that device (the kept
+ * address belongs to the old context).  Errors: TTC_EINVAL (null pointers,
+ * bad ranks), TTC_EUNSUPPORTED (limits above), TTC_ECUDA (launch failure). */
 int ttc_tt_dist2_static(int d, const int64_t* n, const int32_t* ra, const double* const* a_dev,
                         const int32_t* rb, const double* const* b_dev, double* out_dev,
                         void* cuda_stream);

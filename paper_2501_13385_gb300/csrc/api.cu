@@ -388,10 +388,14 @@ int ttc_set_observations(ttc_ctx* c, int64_t N, const int32_t* idx, const double
   ttc_plan_tables(c);
   P.tab32 = nullptr;
   P.tab64 = nullptr;
+  P.ztab32 = nullptr;
+  P.ztab64 = nullptr;
   if (P.tab_total > 0) {
     size_t cnt = (size_t)P.tab_total * c->rank_bucket;
     TTC_TRY(ttc_alloc(c, (void**)&P.tab32, sizeof(float) * cnt, true));
     TTC_TRY(ttc_alloc(c, (void**)&P.tab64, sizeof(double) * cnt, true));
+    TTC_TRY(ttc_alloc(c, (void**)&P.ztab32, sizeof(float) * cnt, true));
+    TTC_TRY(ttc_alloc(c, (void**)&P.ztab64, sizeof(double) * cnt, true));
   }
   c->have_obs = true;
   c->eps_set = false;

@@ -87,6 +87,9 @@ struct DevProb {
   double* E[TTC_MAXM];           // n_k x r_k x r_{k+1}
   double* B1[TTC_MAXM];          // steepest step: update cores at unit step, n_k x r_k x r_{k+1}
   float* B1_32p[TTC_MAXM];       // the same in FP32, padded like core32p (FP32 steps evaluate with it)
+  double* B1_64p[TTC_MAXM];      // the same in FP64, padded like core64p (FP64 steps)
+  float* ztab32;                 // steepest step: the tangent part of the prefix tables' rows (tab32 layout)
+  double* ztab64;                // the same for FP64 steps (tab64 layout)
   double* zw;                    // steepest step: per slice G^{1/(2m)} <Lam B1 Gam, B1> (all modes)
   double* tpart;                 // steepest step: block partials of ||P_Omega Z||^2
   double* g;                     // residual in input order (when keep_residual)
@@ -187,20 +190,94 @@ __device__ __forceinline__ int code_coord(const DevProb& P, const Code& c, int k
   return (int)((c.word(P.cword[k]) >> P.cshift[k]) & ((1u << P.cbits[k]) - 1u));
 }
 
+// One entry of a tensor train in FP64: v <- v C_k(x_k) along the train, with
+// element (i, j) of core k's slice x read through the layout functor
+// (C.at(k, x, i, j), C.r(k) the ranks).  Two rank-sized arrays are live.
+template <typename Cores>
+__device__ __forceinline__ double tt_chain_value(const Cores& C, int d, const int* xs) {
+  double v[TTC_MAXR], t[TTC_MAXR];
+  v[0] = 1.0;
+  for (int k = 0; k < d; ++k) {
+    const int p = C.r(k), q = C.r(k + 1), x = xs[k];
+    for (int j = 0; j < q; ++j) {
+      double a0 = 0.0, a1 = 0.0;
+      int i = 0;
+      for (; i + 1 < p; i += 2) {
+        a0 = fma(v[i], C.at(k, x, i, j), a0);
+        a1 = fma(v[i + 1], C.at(k, x, i + 1, j), a1);
+      }
+      if (i < p) a0 = fma(v[i], C.at(k, x, i, j), a0);
+      t[j] = a0 + a1;
+    }
+    for (int j = 0; j < q; ++j) v[j] = t[j];
+  }
+  return v[0];
+}
+
+// Per-block partial sums of ||A - B||^2 and ||B||^2 over the d* entries
+// (linear index l, last mode fastest) of two tensor trains, every entry
+// evaluated in FP64; the block's sums go to part[2 blockIdx], part[2 blockIdx + 1].
+// blockDim.x must be 256.
+template <typename CoresA, typename CoresB>
+__device__ __forceinline__ void tt_dist_block(const CoresA& A, const CoresB& B, int d, const int* n, long long dstar,
+                                              double* part) {
+  __shared__ double sh1[256];
+  __shared__ double sh2[256];
+  double d2 = 0.0, b2 = 0.0;
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < dstar;
+       l += (long long)gridDim.x * blockDim.x) {
+    int xs[TTC_MAXM];
+    long long t = l;
+    for (int k = d - 1; k >= 0; --k) {
+      xs[k] = (int)(t % n[k]);
+      t /= n[k];
+    }
+    const double va = tt_chain_value(A, d, xs);
+    const double vb = tt_chain_value(B, d, xs);
+    const double df = va - vb;
+    d2 = fma(df, df, d2);
+    b2 = fma(vb, vb, b2);
+  }
+  sh1[threadIdx.x] = d2;
+  sh2[threadIdx.x] = b2;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      sh1[threadIdx.x] += sh1[threadIdx.x + s];
+      sh2[threadIdx.x] += sh2[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sh1[0];
+    part[2 * blockIdx.x + 1] = sh2[0];
+  }
+}
+
 // C (M x N, ldc) = alpha * op(A) * op(B) (+ beta * C when accumulate), on data
 // visible to the whole block; threads stride over the M*N outputs.  The caller
 // synchronises.  op(A) is M x K: A[i*lda + k] or, transposed, A[k*lda + i].
+// The inner sum runs as four independent FMA chains (k mod 4), added at the
+// end: a dependent FP64 FMA costs ~150 cycles on GB300, so one chain per
+// output would leave the pipe idle.
 template <typename T>
 __device__ void blk_gemm(int M, int N, int K, const T* A, int lda, bool ta, const T* B, int ldb,
                          bool tb, T* C, int ldc, T alpha, bool accumulate) {
+  const int sa = ta ? lda : 1, sb = tb ? 1 : ldb;
   for (int idx = threadIdx.x; idx < M * N; idx += blockDim.x) {
     int i = idx / N, j = idx - (idx / N) * N;
-    T acc = 0;
-    for (int k = 0; k < K; ++k) {
-      T a = ta ? A[k * lda + i] : A[i * lda + k];
-      T b = tb ? B[j * ldb + k] : B[k * ldb + j];
-      acc = fma(a, b, acc);
+    const T* a = ta ? A + i : A + i * lda;
+    const T* b = tb ? B + j * ldb : B + j;
+    T c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    int k = 0;
+    for (; k + 3 < K; k += 4) {
+      c0 = fma(a[k * sa], b[k * sb], c0);
+      c1 = fma(a[(k + 1) * sa], b[(k + 1) * sb], c1);
+      c2 = fma(a[(k + 2) * sa], b[(k + 2) * sb], c2);
+      c3 = fma(a[(k + 3) * sa], b[(k + 3) * sb], c3);
     }
+    for (; k < K; ++k) c0 = fma(a[k * sa], b[k * sb], c0);
+    const T acc = (c0 + c1) + (c2 + c3);
     C[i * ldc + j] = accumulate ? fma(alpha, acc, C[i * ldc + j]) : alpha * acc;
   }
 }

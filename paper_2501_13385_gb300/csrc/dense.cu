@@ -266,6 +266,21 @@ __device__ void post_small_proj(const DevProb& P, double* sm) {
   if (threadIdx.x == 0 && flag) atomicOr(P.flags, 2u);
 }
 
+// sum_{t0 <= t < t1} x[t * sx] y[t * sy] with four independent FP64 chains
+// (a dependent FP64 FMA costs ~150 cycles on this GPU)
+__device__ __forceinline__ double dot4(const double* x, int sx, const double* y, int sy, int t0, int t1) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int t = t0;
+  for (; t + 3 < t1; t += 4) {
+    a0 = fma(x[t * sx], y[t * sy], a0);
+    a1 = fma(x[(t + 1) * sx], y[(t + 1) * sy], a1);
+    a2 = fma(x[(t + 2) * sx], y[(t + 2) * sy], a2);
+    a3 = fma(x[(t + 3) * sx], y[(t + 3) * sy], a3);
+  }
+  for (; t < t1; ++t) a0 = fma(x[t * sx], y[t * sy], a0);
+  return (a0 + a1) + (a2 + a3);
+}
+
 // Bond k of the retraction: from N_k (in P.small) and Psi[k+1], P_k and S_k.
 // The top-r left singular vectors of (T^{<=k-1} (x) I)^T W^{<k>} =
 // L(C'_k) C^{>=k+1} are L(C'_k) u, u spanning the dominant r-dimensional
@@ -289,7 +304,7 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
   float* V32 = G32 + qq;
   double* VD = GG + 2 * qq;        // the FP64 basis V (column-major)
   double* red = VD + qq;           // blockDim doubles
-  double* dg = red + bd;           // q doubles
+  double* dg = red + bd;           // 2q doubles
   __shared__ int bad;
   __shared__ int order[TTC_MAXQ];
   __shared__ double scl[2];   // powers of two that scale Psi and N to unit size
@@ -321,13 +336,21 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
     RP[i] = Psi[i] * scl[0];
     RN[i] = N[i] * scl[1];
   }
-  blk_chol2_upper_psd(RN, RP, q);
+  blk_chol2_upper_psd(RN, RP, q, dg);
+  // R_N transposed (into GG for now), so that lanes with consecutive rows
+  // of G read consecutive words below
+  for (int idx = tid; idx < qq; idx += bd) {
+    const int t = idx / q, i = idx - t * q;
+    GG[idx] = RN[i * q + t];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < qq; idx += bd) RN[idx] = GG[idx];
+  __syncthreads();
   // G = R_N R_P^T, column-major: G[i][j] = sum_{t >= max(i, j)} R_N[i][t] R_P[j][t]
   double fro = 0.0;
   for (int idx = tid; idx < qq; idx += bd) {
     const int j = idx / q, i = idx - j * q;
-    double acc = 0.0;
-    for (int t = max(i, j); t < q; ++t) acc = fma(RN[i * q + t], RP[j * q + t], acc);
+    const double acc = dot4(RN + i, q, RP + j * q, 1, max(i, j), q);
     GG[idx] = acc;
     G32[idx] = (float)acc;
     V32[idx] = (i == j) ? 1.f : 0.f;
@@ -344,33 +367,26 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
     __syncthreads();
     for (int idx = tid; idx < qq; idx += bd) {     // E (R_N is not needed any more)
       const int j = idx / q, i = idx - j * q;
-      double acc = (i == j) ? -1.0 : 0.0;
-      for (int t = 0; t < q; ++t) acc = fma(VD[i * q + t], VD[j * q + t], acc);
-      RN[idx] = acc;
+      RN[idx] = dot4(VD + i * q, 1, VD + j * q, 1, 0, q) - ((i == j) ? 1.0 : 0.0);
     }
     __syncthreads();
     double* F = reinterpret_cast<double*>(G32);     // G32 and V32 are not needed any more
     for (int idx = tid; idx < qq; idx += bd) {     // F = I - E/2 + 3/8 E^2
       const int j = idx / q, i = idx - j * q;
-      double acc = 0.0;
-      for (int t = 0; t < q; ++t) acc = fma(RN[t * q + i], RN[j * q + t], acc);
+      const double acc = dot4(RN + i, q, RN + j * q, 1, 0, q);
       F[idx] = fma(0.375, acc, ((i == j) ? 1.0 : 0.0) - 0.5 * RN[idx]);
     }
     __syncthreads();
     for (int idx = tid; idx < qq; idx += bd) {     // V F (into RN: E is not needed any more)
       const int j = idx / q, i = idx - j * q;
-      double acc = 0.0;
-      for (int t = 0; t < q; ++t) acc = fma(VD[t * q + i], F[j * q + t], acc);
-      RN[idx] = acc;
+      RN[idx] = dot4(VD + i, q, F + j * q, 1, 0, q);
     }
     __syncthreads();
     for (int idx = tid; idx < qq; idx += bd) VD[idx] = RN[idx];   // V
     __syncthreads();
     for (int idx = tid; idx < qq; idx += bd) {     // G V (G is not needed afterwards)
       const int j = idx / q, i = idx - j * q;
-      double acc = 0.0;
-      for (int t = 0; t < q; ++t) acc = fma(GG[t * q + i], VD[j * q + t], acc);
-      RN[idx] = acc;
+      RN[idx] = dot4(GG + i, q, VD + j * q, 1, 0, q);
     }
     sweeps += blk_hestenes<double>(RN, VD, q, 1e-14, 1e-30 * fro, 8);
   }
@@ -378,9 +394,12 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
   // squared singular values (column norms), NaN ordered last
   for (int j = tid; j < q; j += bd) {
     double s2 = 0.0;
-    for (int i = 0; i < q; ++i) {
-      const double v = fp64 ? RN[j * q + i] : (double)G32[j * q + i];
-      s2 = fma(v, v, s2);
+    if (fp64) {
+      s2 = dot4(RN + j * q, 1, RN + j * q, 1, 0, q);
+    } else {
+      float f = 0.f;
+      for (int i = 0; i < q; ++i) f = fmaf(G32[j * q + i], G32[j * q + i], f);
+      s2 = f;
     }
     dg[j] = (s2 == s2) ? s2 : -1.0;
   }
@@ -395,12 +414,10 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
   // U = R_P^T w, w the top-r columns of V (q x r, row-major)
   double* U = GG;
   double* W = GG + q * r;
-  for (int idx = tid; idx < q * r; idx += bd) {
-    const int a = idx / r, c = idx - (idx / r) * r;
+  for (int idx = tid; idx < q * r; idx += bd) {   // lanes along a: R_P rows read as consecutive words
+    const int c = idx / q, a = idx - (idx / q) * q;
     const int col = order[c];
-    double acc = 0.0;
-    for (int t = 0; t <= a; ++t) acc = fma(RP[t * q + a], VD[col * q + t], acc);
-    U[idx] = acc;
+    U[a * r + c] = dot4(RP + a, q, VD + col * q, 1, 0, a + 1);
   }
   __syncthreads();
   double* Bm = GG + qq;            // r x r (over G32, V32 and VD, which are not needed any more)
@@ -658,8 +675,14 @@ __device__ __forceinline__ void warp_mm_t(double* Y, const double* X, int ldx, c
   const int lane = threadIdx.x & 31;
   for (int e = lane; e < M * N; e += 32) {
     const int i = e / N, j = e - (e / N) * N;
-    double acc = 0.0;
-    for (int t = 0; t < K; ++t) acc = fma(X[i * ldx + t], Z[t * ldz + j], acc);
+    double a0 = 0.0, a1 = 0.0;   // two chains: a dependent FP64 FMA costs ~150 cycles
+    int t = 0;
+    for (; t + 1 < K; t += 2) {
+      a0 = fma(X[i * ldx + t], Z[t * ldz + j], a0);
+      a1 = fma(X[i * ldx + t + 1], Z[(t + 1) * ldz + j], a1);
+    }
+    if (t < K) a0 = fma(X[i * ldx + t], Z[t * ldz + j], a0);
+    const double acc = a0 + a1;
     Y[e] = kScale ? alpha * acc : acc;
   }
   __syncwarp();
@@ -1020,9 +1043,12 @@ __global__ void __launch_bounds__(128) k_build_B1(const DevProb P) {
   }
   double* out = P.B1[k] + (long long)x * ra * rb;
   float* out32 = P.B1_32p[k] + (long long)x * P.R * P.R;
+  double* out64 = P.B1_64p[k] + (long long)x * P.R * P.R;
   for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
     out[i] = B[i];
-    out32[pad_idx(P, k, i / rb, i - (i / rb) * rb)] = (float)B[i];
+    const int pi = pad_idx(P, k, i / rb, i - (i / rb) * rb);
+    out32[pi] = (float)B[i];
+    out64[pi] = B[i];
   }
   blk_gemm<double>(ra, rb, ra, P.small + P.off_lam[k], ra, false, B, rb, false, t1, rb, 1.0, false);   // Lam B1
   __syncthreads();
@@ -1040,148 +1066,172 @@ __global__ void __launch_bounds__(128) k_build_B1(const DevProb P) {
 
 // ||P_Omega Z||^2 = sum over Omega of (sum_k l_{k-1} B1_k(x_k) r_{k+1})^2: the
 // tangent TT [[T, 0], [B1, T]] evaluated entry by entry along the chain
-// (l_T, l_Z) <- (l_T T_k(x_k), l_Z T_k(x_k) + l_T B1_k(x_k)) in FP64, in the
-// mode-1 order of Omega; block partials, then the last block forms
-// alpha_l = ||Z||_W^2 / ||P_Omega Z||^2 (an explicit step size, when given,
-// is kept).
+//   (l_T, l_Z) <- (l_T T_k(x_k), l_Z T_k(x_k) + l_T B1_k(x_k)),
+// in the precision of the step (FP32 steps: FP32 on the padded FP32 mirrors,
+// squares summed in FP64; the step size only scales the step, so FP32's
+// relative error in alpha moves the iterate by that fraction of one step, as
+// the FP32 sampled pass does).  Where a prefix table covers the first modes,
+// the chain starts from its row (l_T) and the row of its tangent companion
+// table (l_Z), built by k_build_ztables.  Block partials; the last block forms
+// alpha_l = ||Z||_W^2 / ||P_Omega Z||^2 (an explicit step size is kept).
 constexpr int kTanThreads = 256;
 constexpr int kTanCounter = 127;
 
-template <int R>
-__global__ void __launch_bounds__(kTanThreads) k_tangent_sq(const DevProb P, int nslices) {
-  __shared__ double red[kTanThreads];
-  __shared__ int am_last;
-  double acc = 0.0;
-  for (int e = blockIdx.x * kTanThreads + threadIdx.x; e < P.N; e += gridDim.x * kTanThreads) {
-    const Code w = load_code(P, 0, e);
-    double lT[R], lZ[R];
+template <typename T>
+__device__ __forceinline__ const T* pcore(const DevProb& P, int k);
+template <>
+__device__ __forceinline__ const float* pcore<float>(const DevProb& P, int k) { return P.core32p[k]; }
+template <>
+__device__ __forceinline__ const double* pcore<double>(const DevProb& P, int k) { return P.core64p[k]; }
+template <typename T>
+__device__ __forceinline__ const T* pb1(const DevProb& P, int k);
+template <>
+__device__ __forceinline__ const float* pb1<float>(const DevProb& P, int k) { return P.B1_32p[k]; }
+template <>
+__device__ __forceinline__ const double* pb1<double>(const DevProb& P, int k) { return P.B1_64p[k]; }
+template <typename T>
+__device__ __forceinline__ T* ptab(const DevProb& P, bool z);
+template <>
+__device__ __forceinline__ float* ptab<float>(const DevProb& P, bool z) { return z ? P.ztab32 : P.tab32; }
+template <>
+__device__ __forceinline__ double* ptab<double>(const DevProb& P, bool z) { return z ? P.ztab64 : P.tab64; }
+
+// 16-byte loads of a padded row (4 floats or 2 doubles at a time)
+template <int RC>
+__device__ __forceinline__ void ld_row16(const float* p, int len, float (&v)[RC]) {
 #pragma unroll
-    for (int a = 0; a < R; ++a) {
-      lT[a] = 0.0;
-      lZ[a] = 0.0;
-    }
-    lT[0] = 1.0;
-    for (int k = 0; k < P.m; ++k) {
-      const int x = code_coord(P, w, k);
-      const int ra = P.r[k], rb = P.r[k + 1];
-      const double* S = P.core64[k] + (long long)x * ra * rb;
-      const double* Bk = P.B1[k] + (long long)x * ra * rb;
-      double nT[R], nZ[R];
-#pragma unroll
-      for (int b = 0; b < R; ++b) {
-        nT[b] = 0.0;
-        nZ[b] = 0.0;
-        if (b < rb) {
-#pragma unroll
-          for (int a = 0; a < R; ++a) {
-            if (a >= ra) break;
-            const double sv = __ldg(S + a * rb + b);
-            nT[b] = fma(lT[a], sv, nT[b]);
-            nZ[b] = fma(lZ[a], sv, fma(lT[a], __ldg(Bk + a * rb + b), nZ[b]));
-          }
-        }
-      }
-#pragma unroll
-      for (int b = 0; b < R; ++b) {
-        lT[b] = nT[b];
-        lZ[b] = nZ[b];
-      }
-    }
-    acc = fma(lZ[0], lZ[0], acc);
+  for (int b = 0; b < RC; b += 4) {
+    if (b >= len) break;
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p + b));
+    v[b] = t.x;
+    if (b + 1 < RC) v[b + 1] = t.y;
+    if (b + 2 < RC) v[b + 2] = t.z;
+    if (b + 3 < RC) v[b + 3] = t.w;
   }
-  const double tot = blk_sum(acc, red);
-  if (threadIdx.x == 0) P.tpart[blockIdx.x] = tot;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) am_last = (atomicAdd(P.counters + kTanCounter, 1) == (int)gridDim.x - 1);
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  double den = 0.0, num = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += kTanThreads) den += __ldcg(P.tpart + i);
-  den = blk_sum(den, red);
-  for (int i = threadIdx.x; i < nslices; i += kTanThreads) num += __ldcg(P.zw + i);
-  num = blk_sum(num, red);
-  if (threadIdx.x == 0) {
-    if (!(P.scal[SC_ALPHA_OVR] > 0.0)) P.scal[SC_ALPHA] = den > 0.0 ? num / den : 0.0;
-    P.counters[kTanCounter] = 0;
+}
+template <int RC>
+__device__ __forceinline__ void ld_row16(const double* p, int len, double (&v)[RC]) {
+#pragma unroll
+  for (int b = 0; b < RC; b += 2) {
+    if (b >= len) break;
+    const double2 t = __ldg(reinterpret_cast<const double2*>(p + b));
+    v[b] = t.x;
+    if (b + 1 < RC) v[b + 1] = t.y;
   }
 }
 
-// The same sum in an FP32 step: the chain in FP32 on the padded FP32 mirrors
-// of the cores and of B1 (rows of R floats, read as 16-byte vectors), the
-// squares summed in FP64.  The step size only scales the step, so FP32's
-// relative error (~1e-6) in alpha moves the iterate by that fraction of one
-// step, as the FP32 sampled pass does.
-template <int R>
-__global__ void __launch_bounds__(kTanThreads) k_tangent_sq32(const DevProb P, int nslices) {
-  __shared__ double red[kTanThreads];
-  __shared__ int am_last;
-  double acc = 0.0;
-  for (int e = blockIdx.x * kTanThreads + threadIdx.x; e < P.N; e += gridDim.x * kTanThreads) {
-    const Code w = load_code(P, 0, e);
-    float lT[R], lZ[R];
+// (l_T, l_Z) <- (l_T T_j(x), l_Z T_j(x) + l_T B1_j(x)) on the padded mirrors
+// (row stride R), register arrays of RC >= every rank
+template <typename T, int R, int RC>
+__device__ __forceinline__ void tangent_times(const DevProb& P, int j, int x, T (&lT)[RC], T (&lZ)[RC]) {
+  constexpr int V = 16 / sizeof(T);   // values per 16-byte load
+  const int ra = P.r[j], rb = P.r[j + 1];
+  const T* S = pcore<T>(P, j) + (long long)x * R * R;
+  const T* Bk = pb1<T>(P, j) + (long long)x * R * R;
+  T nT[RC], nZ[RC];
 #pragma unroll
-    for (int a = 0; a < R; ++a) {
-      lT[a] = 0.f;
-      lZ[a] = 0.f;
-    }
-    lT[0] = 1.f;
-    for (int k = 0; k < P.m; ++k) {
-      const int x = code_coord(P, w, k);
-      const int ra = P.r[k], rb = P.r[k + 1];
-      const float* S = P.core32p[k] + (long long)x * R * R;
-      const float* Bk = P.B1_32p[k] + (long long)x * R * R;
-      if (rb == 1) {   // the slice is one contiguous column
-        float t = 0.f, z = 0.f;
+  for (int b = 0; b < RC; ++b) {
+    nT[b] = 0;
+    nZ[b] = 0;
+  }
+  if (rb == 1) {   // the slice is one contiguous column
 #pragma unroll
-        for (int a0 = 0; a0 < R; a0 += 4) {
-          if (a0 >= ra) break;
-          const float4 sv = __ldg(reinterpret_cast<const float4*>(S + a0));
-          const float4 bv = __ldg(reinterpret_cast<const float4*>(Bk + a0));
-          const float s4[4] = {sv.x, sv.y, sv.z, sv.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
+    for (int a0 = 0; a0 < RC; a0 += V) {
+      if (a0 >= ra) break;
+      T sv[V], bv[V];
+      ld_row16<V>(S + a0, V, sv);
+      ld_row16<V>(Bk + a0, V, bv);
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            t = fmaf(lT[a0 + i], s4[i], t);
-            z = fmaf(lZ[a0 + i], s4[i], fmaf(lT[a0 + i], b4[i], z));
-          }
-        }
-#pragma unroll
-        for (int b = 0; b < R; ++b) {
-          lT[b] = b == 0 ? t : 0.f;
-          lZ[b] = b == 0 ? z : 0.f;
-        }
-      } else {
-        float nT[R], nZ[R];
-#pragma unroll
-        for (int b = 0; b < R; ++b) {
-          nT[b] = 0.f;
-          nZ[b] = 0.f;
-        }
-#pragma unroll
-        for (int a = 0; a < R; ++a) {
-          if (a >= ra) break;
-          const float la = lT[a], za = lZ[a];
-#pragma unroll
-          for (int b0 = 0; b0 < R; b0 += 4) {
-            if (b0 >= rb) break;
-            const float4 sv = __ldg(reinterpret_cast<const float4*>(S + a * R + b0));
-            const float4 bv = __ldg(reinterpret_cast<const float4*>(Bk + a * R + b0));
-            const float s4[4] = {sv.x, sv.y, sv.z, sv.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              nT[b0 + i] = fmaf(la, s4[i], nT[b0 + i]);
-              nZ[b0 + i] = fmaf(za, s4[i], fmaf(la, b4[i], nZ[b0 + i]));
-            }
-          }
-        }
-#pragma unroll
-        for (int b = 0; b < R; ++b) {
-          lT[b] = nT[b];
-          lZ[b] = nZ[b];
+      for (int i = 0; i < V; ++i) {
+        if (a0 + i < RC) {
+          nT[0] = fma(lT[a0 + i], sv[i], nT[0]);
+          nZ[0] = fma(lZ[a0 + i], sv[i], fma(lT[a0 + i], bv[i], nZ[0]));
         }
       }
     }
+  } else {
+#pragma unroll
+    for (int a = 0; a < RC; ++a) {
+      if (a >= ra) break;
+      const T la = lT[a], za = lZ[a];
+#pragma unroll
+      for (int b0 = 0; b0 < RC; b0 += V) {
+        if (b0 >= rb) break;
+        T sv[V], bv[V];
+        ld_row16<V>(S + a * R + b0, V, sv);
+        ld_row16<V>(Bk + a * R + b0, V, bv);
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+          if (b0 + i < RC) {
+            nZ[b0 + i] = fma(za, sv[i], fma(la, bv[i], nZ[b0 + i]));
+            nT[b0 + i] = fma(la, sv[i], nT[b0 + i]);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < RC; ++b) {
+    lT[b] = nT[b];
+    lZ[b] = nZ[b];
+  }
+}
+
+// The tangent companion of the prefix tables: row i of ztab holds l_Z over
+// the table's modes (the prefix table itself holds l_T), one thread per row.
+template <typename T, int R, int RC>
+__global__ void __launch_bounds__(128) k_build_ztables(const DevProb P) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < P.tab_total;
+       g += (long long)gridDim.x * blockDim.x) {
+    int t = 0;
+    while (t + 1 < P.ntab && g >= P.tab_row0[t + 1]) ++t;
+    if (P.tab_side[t] != 0) continue;   // suffix tables have no companion
+    const unsigned row = (unsigned)(g - P.tab_row0[t]);
+    const int jt = P.tab_j[t];
+    T lT[RC], lZ[RC];
+#pragma unroll
+    for (int a = 0; a < RC; ++a) {
+      lT[a] = 0;
+      lZ[a] = 0;
+    }
+    lT[0] = 1;
+    bool valid = true;
+    for (int j = 0; j < jt; ++j) {
+      const int x = (int)((row >> (P.cshift[j] - P.tab_shift[t])) & ((1u << P.cbits[j]) - 1u));
+      valid = valid && x < P.n[j];
+      if (valid) tangent_times<T, R, RC>(P, j, x, lT, lZ);
+    }
+    T* dst = ptab<T>(P, true) + g * R;
+#pragma unroll
+    for (int a = 0; a < R; ++a) dst[a] = (valid && a < RC && a < P.r[jt]) ? lZ[a < RC ? a : 0] : T(0);
+  }
+}
+
+template <typename T, int R, int RC>
+__global__ void __launch_bounds__(kTanThreads) k_tangent_sq(const DevProb P, int nslices) {
+  __shared__ double red[kTanThreads];
+  __shared__ int am_last;
+  // the longest prefix table: rows of l_T and l_Z over modes < j0
+  const int tp = P.m >= 2 ? P.pre_tab[P.m - 1] : -1;
+  const int j0 = tp >= 0 ? P.tab_j[tp] : 0;
+  double acc = 0.0;
+  for (int e = blockIdx.x * kTanThreads + threadIdx.x; e < P.N; e += gridDim.x * kTanThreads) {
+    const Code w = load_code(P, 0, e);
+    T lT[RC], lZ[RC];
+#pragma unroll
+    for (int a = 0; a < RC; ++a) {
+      lT[a] = 0;
+      lZ[a] = 0;
+    }
+    if (tp >= 0) {
+      const long long row =
+          P.tab_row0[tp] + (long long)((w.word(P.tab_word[tp]) >> P.tab_shift[tp]) & ((1u << P.tab_bits[tp]) - 1u));
+      ld_row16<RC>(ptab<T>(P, false) + row * R, RC, lT);
+      ld_row16<RC>(ptab<T>(P, true) + row * R, RC, lZ);
+    } else {
+      lT[0] = 1;
+    }
+    for (int k = j0; k < P.m; ++k) tangent_times<T, R, RC>(P, k, code_coord(P, w, k), lT, lZ);
     acc = fma((double)lZ[0], (double)lZ[0], acc);
   }
   const double tot = blk_sum(acc, red);
@@ -1273,56 +1323,20 @@ __global__ void k_copy_cores(const DevProb P, int to_prev) {
 }
 
 // ---- metrics: dense form for small d* (every entry, FP64) -------------------
-__global__ void k_dense_diff(const DevProb P, int which, long long dstar, double* part) {
-  __shared__ double sh1[256];
-  __shared__ double sh2[256];
-  double d2 = 0.0, b2 = 0.0;
-  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < dstar; l += (long long)gridDim.x * blockDim.x) {
-    int xs[TTC_MAXM];
-    long long t = l;
-    for (int k = P.m - 1; k >= 0; --k) {
-      xs[k] = (int)(t % P.n[k]);
-      t /= P.n[k];
-    }
-    double va[TTC_MAXR], vb[TTC_MAXR], tmp[TTC_MAXR];
-    va[0] = 1.0;
-    vb[0] = 1.0;
-    for (int k = 0; k < P.m; ++k) {
-      int ra = P.r[k], rb = P.r[k + 1];
-      const double* M = P.core64[k] + (long long)xs[k] * ra * rb;
-      for (int b = 0; b < rb; ++b) {
-        double acc = 0.0;
-        for (int a = 0; a < ra; ++a) acc = fma(va[a], M[a * rb + b], acc);
-        tmp[b] = acc;
-      }
-      for (int b = 0; b < rb; ++b) va[b] = tmp[b];
-      int sa = which == 0 ? P.rt[k] : P.r[k], sb = which == 0 ? P.rt[k + 1] : P.r[k + 1];
-      const double* Mb = (which == 0 ? P.truth[k] : P.prev64[k]) + (long long)xs[k] * sa * sb;
-      for (int b = 0; b < sb; ++b) {
-        double acc = 0.0;
-        for (int a = 0; a < sa; ++a) acc = fma(vb[a], Mb[a * sb + b], acc);
-        tmp[b] = acc;
-      }
-      for (int b = 0; b < sb; ++b) vb[b] = tmp[b];
-    }
-    double d = va[0] - vb[0];
-    d2 = fma(d, d, d2);
-    b2 = fma(vb[0], vb[0], b2);
+// cores in the library's slice-major layout: T_k(x) an r_k x r_{k+1} block
+struct SliceMajorCores {
+  const double* const* core;
+  const int* rk;
+  __device__ __forceinline__ int r(int k) const { return rk[k]; }
+  __device__ __forceinline__ double at(int k, int x, int i, int j) const {
+    return core[k][((long long)x * rk[k] + i) * rk[k + 1] + j];
   }
-  sh1[threadIdx.x] = d2;
-  sh2[threadIdx.x] = b2;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      sh1[threadIdx.x] += sh1[threadIdx.x + s];
-      sh2[threadIdx.x] += sh2[threadIdx.x + s];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = sh1[0];
-    part[2 * blockIdx.x + 1] = sh2[0];
-  }
+};
+
+__global__ void __launch_bounds__(256) k_dense_diff(const DevProb P, int which, long long dstar, double* part) {
+  const SliceMajorCores A{P.core64, P.r};
+  const SliceMajorCores B{which == 0 ? P.truth : P.prev64, which == 0 ? P.rt : P.r};
+  tt_dist_block(A, B, P.m, P.n, dstar, part);
 }
 
 __global__ void k_dense_diff_finish(const DevProb P, const double* part, int nb) {
@@ -1455,10 +1469,14 @@ int ttc_alloc_dense(ttc_ctx* c) {
       TTC_TRY(ttc_alloc(c, (void**)&b1, sizeof(double) * (size_t)c->n[k] * c->r[k] * c->r[k + 1], false));
       P.B1[k] = b1;
       float* b32 = nullptr;
+      double* b64 = nullptr;
       const size_t padcnt = (size_t)c->n[k] * c->rank_bucket * c->rank_bucket;
       TTC_TRY(ttc_alloc(c, (void**)&b32, sizeof(float) * padcnt, false));
+      TTC_TRY(ttc_alloc(c, (void**)&b64, sizeof(double) * padcnt, false));
       TTC_CUDA(cudaMemsetAsync(b32, 0, sizeof(float) * padcnt, c->stream));   // the padding stays zero
+      TTC_CUDA(cudaMemsetAsync(b64, 0, sizeof(double) * padcnt, c->stream));
       P.B1_32p[k] = b32;
+      P.B1_64p[k] = b64;
       nsl += c->n[k];
     }
     TTC_TRY(ttc_alloc(c, (void**)&P.zw, sizeof(double) * (size_t)nsl, false));
@@ -1610,6 +1628,41 @@ int ttc_alloc_dense(ttc_ctx* c) {
   return TTC_OK;
 }
 
+// the steepest step's ||P_Omega Z||^2: the tangent companion tables (when
+// prefix tables exist), then the evaluation over Omega
+template <typename T>
+int launch_tangent(ttc_ctx* c, int tb, int nslices, cudaStream_t st) {
+  const DevProb& P = c->hp;
+  const int R = c->rank_bucket;
+  const bool r24 = c->rank_max <= 24;   // register arrays of 24 suffice for ranks <= 24 in bucket 32
+  if (P.ntab > 0 && P.m >= 2 && P.pre_tab[P.m - 1] >= 0) {
+    const int zb = (int)std::min<long long>((P.tab_total + 127) / 128, 4 * 152);
+    switch (R) {
+      case 4: k_build_ztables<T, 4, 4><<<zb, 128, 0, st>>>(P); break;
+      case 8: k_build_ztables<T, 8, 8><<<zb, 128, 0, st>>>(P); break;
+      case 16: k_build_ztables<T, 16, 16><<<zb, 128, 0, st>>>(P); break;
+      default:
+        if (r24) k_build_ztables<T, 32, 24><<<zb, 128, 0, st>>>(P);
+        else k_build_ztables<T, 32, 32><<<zb, 128, 0, st>>>(P);
+        break;
+    }
+    TTC_CUDA(cudaGetLastError());
+    c->nlaunch += 1;
+  }
+  switch (R) {
+    case 4: k_tangent_sq<T, 4, 4><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+    case 8: k_tangent_sq<T, 8, 8><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+    case 16: k_tangent_sq<T, 16, 16><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
+    default:
+      if (r24) k_tangent_sq<T, 32, 24><<<tb, kTanThreads, 0, st>>>(P, nslices);
+      else k_tangent_sq<T, 32, 32><<<tb, kTanThreads, 0, st>>>(P, nslices);
+      break;
+  }
+  TTC_CUDA(cudaGetLastError());
+  c->nlaunch += 2;   // with k_build_B1
+  return TTC_OK;
+}
+
 int ttc_launch_dense(ttc_ctx* c) {
   const DevProb& P = c->hp;
   const int m = c->m;
@@ -1623,22 +1676,10 @@ int ttc_launch_dense(ttc_ctx* c) {
     TTC_CUDA(cudaGetLastError());
     const int tb = tangent_blocks(P);
     if (P.bond_fp64) {   // an FP64 step: ||P_Omega Z||^2 in FP64
-      switch (c->rank_bucket) {
-        case 4: k_tangent_sq<4><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
-        case 8: k_tangent_sq<8><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
-        case 16: k_tangent_sq<16><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
-        default: k_tangent_sq<32><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
-      }
+      TTC_TRY(launch_tangent<double>(c, tb, nslices, st));
     } else {
-      switch (c->rank_bucket) {
-        case 4: k_tangent_sq32<4><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
-        case 8: k_tangent_sq32<8><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
-        case 16: k_tangent_sq32<16><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
-        default: k_tangent_sq32<32><<<tb, kTanThreads, 0, st>>>(P, nslices); break;
-      }
+      TTC_TRY(launch_tangent<float>(c, tb, nslices, st));
     }
-    TTC_CUDA(cudaGetLastError());
-    c->nlaunch += 2;
   }
   if (pl.warp)
     k_build_C_w<<<(nslices + kWarpsW - 1) / kWarpsW, kThreads, sizeof(double) * kWarpsW * 3 * wscr_mat_host(P), st>>>(

@@ -142,19 +142,28 @@ static __device__ int warp_chol_inv32(const double* A, int lda, int n, float* L,
   return bad;
 }
 
-// C (M x N, ldc) = alpha op(A) op(B) (+ C when accumulate) by one warp.
+// C (M x N, ldc) = alpha op(A) op(B) (+ C when accumulate) by one warp.  Four
+// independent FMA chains per output (k mod 4): a dependent FP64 FMA costs
+// ~150 cycles on this GPU.
 template <typename T>
 __device__ void warp_gemm(int M, int N, int K, const T* A, int lda, bool ta, const T* B, int ldb, bool tb, T* C,
                           int ldc, T alpha, bool accumulate) {
   const int lane = threadIdx.x & 31;
+  const int sa = ta ? lda : 1, sb = tb ? 1 : ldb;
   for (int idx = lane; idx < M * N; idx += 32) {
     int i = idx / N, j = idx - (idx / N) * N;
-    T acc = 0;
-    for (int k = 0; k < K; ++k) {
-      T a = ta ? A[k * lda + i] : A[i * lda + k];
-      T b = tb ? B[j * ldb + k] : B[k * ldb + j];
-      acc = fma(a, b, acc);
+    const T* a = ta ? A + i : A + i * lda;
+    const T* b = tb ? B + j * ldb : B + j;
+    T c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    int k = 0;
+    for (; k + 3 < K; k += 4) {
+      c0 = fma(a[k * sa], b[k * sb], c0);
+      c1 = fma(a[(k + 1) * sa], b[(k + 1) * sb], c1);
+      c2 = fma(a[(k + 2) * sa], b[(k + 2) * sb], c2);
+      c3 = fma(a[(k + 3) * sa], b[(k + 3) * sb], c3);
     }
+    for (; k < K; ++k) c0 = fma(a[k * sa], b[k * sb], c0);
+    const T acc = (c0 + c1) + (c2 + c3);
     C[i * ldc + j] = accumulate ? fma(alpha, acc, C[i * ldc + j]) : alpha * acc;
   }
   __syncwarp();
@@ -264,15 +273,16 @@ static __device__ void blk_chol_linv64(const double* G, int ldg, int n, double* 
 
 // Upper Cholesky factors of two symmetric positive semidefinite n x n
 // matrices (row-major, n <= 64) at once, in place: A = R_A^T R_A and
-// B = R_B^T R_B.  Right-looking, two barriers per pivot: row j of the factor
-// (the Schur complement's row j over its pivot's square root), then the
-// update of the upper triangle of the trailing block by that row's outer
-// product.  A pivot at or below 1e-14 of the largest diagonal entry is
-// rounding noise of a numerically singular Gram (its square root would turn
-// noise of 1e-16 into rows of size 1e-8): it gives a zero row, which keeps
-// R^T R equal to the matrix on its numerical range.  The strict lower
-// triangles are zeroed.
-static __device__ void blk_chol2_upper_psd(double* A, double* B, int n) {
+// B = R_B^T R_B.  Right-looking, one barrier per pivot: the Schur
+// complement is updated whole (both triangles), so the update of pivot j
+// reads column j below the diagonal while row j is scaled into the factor.
+// Each thread keeps fixed (row, column) offsets, so no integer division runs
+// inside the pivot loop.  A pivot at or below 1e-14 of the largest diagonal
+// entry is rounding noise of a numerically singular Gram (its square root
+// would turn noise of 1e-16 into rows of size 1e-8): it gives a zero row,
+// which keeps R^T R equal to the matrix on its numerical range.  The strict
+// lower triangles are zeroed.  diag: 2n doubles.
+static __device__ void blk_chol2_upper_psd(double* A, double* B, int n, double* diag) {
   const int tid = threadIdx.x, bd = blockDim.x;
   __syncthreads();
   double ma = 0.0, mb = 0.0;
@@ -281,34 +291,31 @@ static __device__ void blk_chol2_upper_psd(double* A, double* B, int n) {
     mb = fmax(mb, B[i * n + i]);
   }
   const double ta = 1e-14 * ma, tb = 1e-14 * mb;
+  // half the threads per matrix; within a half, thread h owns columns
+  // c = h mod 64 + 64 w and rows i = h div 64 + rs v of the trailing block
+  const int half = bd / 2, second = tid >= half, h = second ? tid - half : tid;
+  double* M = second ? B : A;
+  const double tm = second ? tb : ta;
+  const int c0 = h & 63, i0 = h >> 6, rs = max(1, half >> 6);
   for (int j = 0; j < n; ++j) {
-    const double da = A[j * n + j], db = B[j * n + j];
-    const double ra = (da > ta) ? rsqrt(da) : 0.0;
-    const double rb = (db > tb) ? rsqrt(db) : 0.0;
-    const int t = n - j;   // row j from the diagonal on
-    for (int idx = tid; idx < 2 * t; idx += bd) {
-      const bool second = idx >= t;
-      const int c = j + (second ? idx - t : idx);
-      double* M = second ? B : A;
-      const double rr = second ? rb : ra;
-      M[j * n + c] = (c == j) ? (second ? db : da) * rr : M[j * n + c] * rr;
+    const double d = M[j * n + j];
+    const double rr = (d > tm) ? rsqrt(d) : 0.0;
+    const double r2 = rr * rr;
+    for (int c = j + 1 + c0; c < n; c += 64) {
+      const double mcj = M[c * n + j] * r2;
+      for (int i = j + 1 + i0; i < n; i += rs) M[i * n + c] = fma(-M[i * n + j], mcj, M[i * n + c]);
     }
-    __syncthreads();
-    const int u = n - 1 - j;   // trailing block, upper triangle by rows
-    for (int idx = tid; idx < 2 * u * u; idx += bd) {
-      const bool second = idx >= u * u;
-      const int e = second ? idx - u * u : idx;
-      const int i = j + 1 + e / u, c = j + 1 + (e - (e / u) * u);
-      if (c < i) continue;
-      double* M = second ? B : A;
-      M[i * n + c] = fma(-M[j * n + i], M[j * n + c], M[i * n + c]);
-    }
+    if (h == 0) diag[(second ? n : 0) + j] = d * rr;   // sqrt(d), or 0
+    for (int c = j + 1 + h; c < n; c += half) M[j * n + c] *= rr;
     __syncthreads();
   }
   for (int idx = tid; idx < 2 * n * n; idx += bd) {
-    const bool second = idx >= n * n;
-    const int e = second ? idx - n * n : idx;
-    if (e % n < e / n) (second ? B : A)[e] = 0.0;
+    const bool sb = idx >= n * n;
+    const int e = sb ? idx - n * n : idx;
+    const int i = e / n, c = e - (e / n) * n;
+    double* X = sb ? B : A;
+    if (c < i) X[e] = 0.0;
+    else if (c == i) X[e] = diag[(sb ? n : 0) + i];
   }
   __syncthreads();
 }
@@ -341,11 +348,20 @@ static __device__ int blk_hestenes(T* G, T* V, int n, T tol, T floor, int max_sw
   const int sub = lane & (lp - 1);
   const int n2 = n + (n & 1), np = n2 / 2;
   const int passes = (np + nslots - 1) / nslots;
-  __shared__ int rotated;
+  // the round-robin pairs (p < q) of every round, once: integer division is
+  // slow, and the rounds are latency-bound
+  __shared__ unsigned char pairs[2 * 63 * 32];
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < (n2 - 1) * np; idx += blockDim.x) {
+    const int t = idx / np, i = idx - t * np;
+    const int pa = (i == 0) ? 0 : ((i - 1 + t) % (n2 - 1)) + 1;
+    const int pb = ((n2 - 2 - i + t) % (n2 - 1)) + 1;
+    pairs[2 * idx] = (unsigned char)min(pa, pb);
+    pairs[2 * idx + 1] = (unsigned char)max(pa, pb);
+  }
   int sweep = 0;
   while (sweep < max_sweeps) {
-    __syncthreads();
-    if (threadIdx.x == 0) rotated = 0;
+    int mine = 0;   // this thread rotated in this sweep
     __syncthreads();
     for (int t = 0; t < n2 - 1; ++t) {
       for (int pass = 0; pass < passes; ++pass) {
@@ -353,10 +369,8 @@ static __device__ int blk_hestenes(T* G, T* V, int n, T tol, T floor, int max_sw
         int p = 0, q = 0;
         bool act = false;
         if (i < np) {
-          const int pa = (i == 0) ? 0 : ((i - 1 + t) % (n2 - 1)) + 1;
-          const int pb = ((n2 - 2 - i + t) % (n2 - 1)) + 1;
-          p = min(pa, pb);
-          q = max(pa, pb);
+          p = pairs[2 * (t * np + i)];
+          q = pairs[2 * (t * np + i) + 1];
           act = q < n;   // not the dummy column of an odd n
         }
         constexpr int MR = 8;   // rows per lane: n <= 16 with lp = 4, n <= 64 with lp = 8
@@ -379,10 +393,22 @@ static __device__ int blk_hestenes(T* G, T* V, int n, T tol, T floor, int max_sw
         // a column below the floor is zero to the working precision: its
         // direction is noise and never settles, so it is not rotated
         if (act && fmin(al, be) > floor && fabs(ga) > tol * sqrt(al * be)) {
-          const T z = (be - al) / (T(2) * ga);
-          const T az = fabs(z);
-          const T tt = az > T(1e15) ? T(0.5) / z : copysign(T(1), z) / (az + sqrt(fma(z, z, T(1))));
-          const T cs = rsqrt(fma(tt, tt, T(1))), sn = cs * tt;
+          T tt, cs;
+          if constexpr (sizeof(T) == 4) {
+            // FP32 sweeps: the angle needs no correct rounding (a rotation
+            // by a slightly different angle is still orthogonal and the
+            // next sweep removes what it leaves), so fast reciprocals
+            const float z = __fdividef(be - al, 2.f * ga);
+            const float az = fabsf(z);
+            tt = az > 1e15f ? __fdividef(0.5f, z) : copysignf(__frcp_rn(az + sqrtf(fmaf(z, z, 1.f))), z);
+            cs = rsqrtf(fmaf(tt, tt, 1.f));
+          } else {
+            const T z = (be - al) / (T(2) * ga);
+            const T az = fabs(z);
+            tt = az > T(1e15) ? T(0.5) / z : copysign(T(1), z) / (az + sqrt(fma(z, z, T(1))));
+            cs = rsqrt(fma(tt, tt, T(1)));
+          }
+          const T sn = cs * tt;
 #pragma unroll
           for (int h = 0; h < MR; ++h) {
             const int row = sub + h * lp;
@@ -394,15 +420,13 @@ static __device__ int blk_hestenes(T* G, T* V, int n, T tol, T floor, int max_sw
               V[q * n + row] = fma(sn, x, cs * y);
             }
           }
-          if (sub == 0) rotated = 1;
+          mine = 1;
         }
       }
       __syncthreads();
     }
     ++sweep;
-    const int any = rotated;
-    __syncthreads();
-    if (!any) break;
+    if (!__syncthreads_or(mine)) break;
   }
   return sweep;
 }

@@ -20,6 +20,8 @@ namespace {
 constexpr int kStaticBlocks = 1024;      // maximum number of blocks (partials) per call
 constexpr int kStaticThreads = 256;
 constexpr long long kMaxEntries = 1LL << 32;   // largest d* accepted (every entry is evaluated)
+constexpr double kMaxWork = 17179869184.0;      // largest FP64 FMA count accepted, 2^34 (d* times the
+                                                // chain products of one entry of A and of B)
 
 // Scratch: two doubles (sum of squared differences, sum of squares of B) per
 // block.  Every GPU that loads the library holds these 16 KiB until exit.
@@ -34,56 +36,21 @@ struct TTPair {
   const double* b[TTC_MAXM];
 };
 
+// cores in the layout of the C ABI: core k is ra[k] x n[k] x ra[k+1], row-major
+struct HostLayoutCores {
+  const double* const* core;
+  const int* rk;
+  const int* nk;
+  __device__ __forceinline__ int r(int k) const { return rk[k]; }
+  __device__ __forceinline__ double at(int k, int x, int i, int j) const {
+    return core[k][((long long)i * nk[k] + x) * rk[k + 1] + j];
+  }
+};
+
 __global__ void __launch_bounds__(kStaticThreads) k_dist_partial(const TTPair T, long long dstar, double* scratch) {
-  __shared__ double s1[kStaticThreads];
-  __shared__ double s2[kStaticThreads];
-  double d2 = 0.0, b2 = 0.0;
-  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < dstar;
-       l += (long long)gridDim.x * blockDim.x) {
-    int xs[TTC_MAXM];
-    long long t = l;
-    for (int k = T.d - 1; k >= 0; --k) {
-      xs[k] = (int)(t % T.n[k]);
-      t /= T.n[k];
-    }
-    double va[TTC_MAXR], vb[TTC_MAXR], tmp[TTC_MAXR];
-    va[0] = 1.0;
-    vb[0] = 1.0;
-    for (int k = 0; k < T.d; ++k) {
-      const int n = T.n[k], x = xs[k];
-      const int p = T.ra[k], q = T.ra[k + 1];
-      for (int j = 0; j < q; ++j) {
-        double acc = 0.0;
-        for (int i = 0; i < p; ++i) acc = fma(va[i], T.a[k][((long long)i * n + x) * q + j], acc);
-        tmp[j] = acc;
-      }
-      for (int j = 0; j < q; ++j) va[j] = tmp[j];
-      const int pb = T.rb[k], qb = T.rb[k + 1];
-      for (int j = 0; j < qb; ++j) {
-        double acc = 0.0;
-        for (int i = 0; i < pb; ++i) acc = fma(vb[i], T.b[k][((long long)i * n + x) * qb + j], acc);
-        tmp[j] = acc;
-      }
-      for (int j = 0; j < qb; ++j) vb[j] = tmp[j];
-    }
-    double diff = va[0] - vb[0];
-    d2 = fma(diff, diff, d2);
-    b2 = fma(vb[0], vb[0], b2);
-  }
-  s1[threadIdx.x] = d2;
-  s2[threadIdx.x] = b2;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) {
-      s1[threadIdx.x] += s1[threadIdx.x + s];
-      s2[threadIdx.x] += s2[threadIdx.x + s];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    scratch[2 * blockIdx.x] = s1[0];
-    scratch[2 * blockIdx.x + 1] = s2[0];
-  }
+  const HostLayoutCores A{T.a, T.ra, T.n};
+  const HostLayoutCores B{T.b, T.rb, T.n};
+  tt_dist_block(A, B, T.d, T.n, dstar, scratch);
 }
 
 // sums the partials of this call in block order (every slot < nb was written
@@ -154,6 +121,11 @@ extern "C" int ttc_tt_dist2_static(int d, const int64_t* n, const int32_t* ra, c
     T.ra[k] = ra[k];
     T.rb[k] = rb[k];
   }
+  // bound the work, not only d*: a rank-32 train of many small modes would
+  // otherwise keep the GPU busy for minutes
+  double per_entry = 0.0;
+  for (int k = 0; k < d; ++k) per_entry += (double)ra[k] * ra[k + 1] + (double)rb[k] * rb[k + 1];
+  if ((double)dstar * per_entry > kMaxWork) return TTC_EUNSUPPORTED;
   double* scratch = nullptr;
   int s = scratch_for_current_device(&scratch);
   if (s != TTC_OK) return s;

@@ -22,11 +22,15 @@ pytestmark = pytest.mark.gpu
 
 
 def _static_dist2(n, ra, a_cores, rb, b_cores, torch):
-    """Calls the C ABI with device copies of the cores; returns (||A-B||^2, ||B||^2)."""
+    """Calls the C ABI with device copies of the cores; returns (||A-B||^2, ||B||^2).
+    PyTorch's allocator holds the same bytes before and after the call (the
+    call takes no memory from it)."""
     dev = torch.device("cuda:0")
     a_t = [torch.from_numpy(np.ascontiguousarray(c)).to(dev) for c in a_cores]
     b_t = [torch.from_numpy(np.ascontiguousarray(c)).to(dev) for c in b_cores]
     out = torch.full((2,), float("nan"), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    held = torch.cuda.memory_allocated(dev)
     d = len(n)
     n_a = np.asarray(n, dtype=np.int64)
     ra_a = np.asarray(ra, dtype=np.int32)
@@ -40,6 +44,7 @@ def _static_dist2(n, ra, a_cores, rb, b_cores, torch):
                                        C.c_void_p(out.data_ptr()), C.c_void_p(stream.cuda_stream))
     assert st == 0, ttc.lib().ttc_strerror(st)
     torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated(dev) == held
     res = out.cpu().numpy()
     return float(res[0]), float(res[1])
 
@@ -79,4 +84,35 @@ def test_static_scratch_rejects_shapes_beyond_its_limits():
     st = L.ttc_tt_dist2_static(d, n_small.ctypes.data_as(C.POINTER(C.c_int64)),
                                r_big.ctypes.data_as(C.POINTER(C.c_int32)), ptrs,
                                r.ctypes.data_as(C.POINTER(C.c_int32)), ptrs, C.c_void_p(1), None)
+    assert st == -10
+
+
+def test_static_scratch_grid_stride_shape_then_a_smaller_one():
+    """d* = 64 * 64 * 96 = 393 216 entries: more than 1024 blocks' worth, so
+    every block strides over the entries and the finish sums 1024 partials;
+    then a smaller shape (fewer blocks) whose call must not read the first
+    call's extra slots.  Against the oracle's distance and norm to 1e-10."""
+    torch = pytest.importorskip("torch")
+    from paper_2501_13385_gb300 import build
+    build.build()
+    for (n, ra, rb, seed) in (([64, 64, 96], [1, 8, 8, 1], [1, 3, 5, 1], 31), ([6, 7, 5], [1, 2, 3, 1], [1, 3, 2, 1], 32)):
+        A = w.random_problem(seed, n, ra, 10, init_rel=0.0).truth
+        B = w.random_problem(seed + 100, n, rb, 10, init_rel=0.0).truth
+        d2, b2 = _static_dist2(n, ra, A, rb, B, torch)
+        assert math.sqrt(d2) == pytest.approx(o.tt_dist(A, B), rel=1e-10)
+        assert math.sqrt(b2) == pytest.approx(o.tt_norm(B), rel=1e-10)
+
+
+def test_static_scratch_rejects_work_beyond_its_budget():
+    """d* = 4^16 = 2^32 entries of rank-32 trains: far more than 2^34 FMAs."""
+    pytest.importorskip("torch")
+    from paper_2501_13385_gb300 import build
+    build.build()
+    L = ttc.lib()
+    d = 16
+    n = np.asarray([4] * d, dtype=np.int64)
+    r = np.asarray([1] + [32] * (d - 1) + [1], dtype=np.int32)
+    ptrs = (C.c_void_p * d)(*([1] * d))                   # never dereferenced: rejected first
+    st = L.ttc_tt_dist2_static(d, n.ctypes.data_as(C.POINTER(C.c_int64)), r.ctypes.data_as(C.POINTER(C.c_int32)),
+                               ptrs, r.ctypes.data_as(C.POINTER(C.c_int32)), ptrs, C.c_void_p(1), None)
     assert st == -10

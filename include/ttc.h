@@ -87,6 +87,17 @@ enum {
   TTC_RETRACT_WEIGHTED = 1 /* T_{l+1} = W^{-1/2} SVD^tt_r(W^{1/2} W_l) (Remark 3.6) */
 };
 
+/* Arithmetic of the dense stages' slice products (the Grams Lam, Gam, H, Psi, N of Lemma 3.5's
+ * projection and Algorithm 1's rounding, and the new cores) when some core rank exceeds 8; the small
+ * factorizations (Gram inverses, the bonds' Cholesky factors and SVDs) are not affected. */
+enum {
+  TTC_DENSE_AUTO = 0, /* FP64 in FP64 steps, float-float in FP32 steps (default) */
+  TTC_DENSE_FP64 = 1, /* always FP64 */
+  TTC_DENSE_FF = 2    /* always float-float: pairs of floats (48-bit significands) with compensated dot
+                         products (Ogita-Rump-Oishi Dot2), ~1e-11 relative to sum |a_i b_i|, FP32's
+                         exponent range; on the FP32 pipe, which on GB300 runs ~6x faster per FMA */
+};
+
 typedef struct {
   int precision;        /* TTC_PREC_* */
   double eps_rel;       /* eps_l = eps_rel * ||G_l||_F^2 / min_k n_k (reading of Section 3.2) */
@@ -105,7 +116,10 @@ typedef struct {
                            (near convergence; needed when noise keeps the residual from falling) */
   int step_fallback;    /* nonzero (default): a solve with the constant step switches to the steepest
                            step for its remaining iterations once the residual norm grows by more
-                           than 2x in one iteration (the constant's scale diverges on that problem) */
+                           than 2x from one read-back to the next (the constant's scale diverges on
+                           that problem); the residual is read back every iteration in MIXED mode
+                           or with the residual rule, else every check_every iterations */
+  int dense_mode;       /* TTC_DENSE_* */
 } ttc_options;
 
 typedef struct {
@@ -133,7 +147,9 @@ typedef struct {
 void ttc_default_options(ttc_options* opt);
 
 /* Create a context for order d (1 < d <= 16), mode sizes n[d] (n_k >= 1),
- * TT-ranks r[d+1] with r[0] = r[d] = 1 and 1 <= r[k] <= 32.  `opt` may be
+ * TT-ranks r[d+1] with r[0] = r[d] = 1, 1 <= r[k] <= 32 and
+ * r[k] <= min(n_1 ... n_k, n_{k+1} ... n_d) (the dimensions of the k-th
+ * unfolding; a larger rank is TTC_EINVAL).  `opt` may be
  * NULL (defaults).  `cuda_stream` (a cudaStream_t, may be NULL) is the stream
  * all work of this context is issued on; NULL makes the context create its
  * own.  On success *out owns the context; free it with ttc_destroy. */
@@ -320,6 +336,9 @@ typedef struct {
   double busy_ms;             /* engine time spent in ticks (step + stop checks) */
   double wall_ms;             /* time since creation */
   double p50_ms, p99_ms, max_ms;   /* latency percentiles of completed requests */
+  int64_t rebuilds;           /* batch graph (re)captures: the member set or a member's precision changed */
+  double rebuild_ms;          /* engine time spent in them (part of busy_ms) */
+  double admit_ms;            /* engine time spent admitting requests (context, layout, uploads) */
 } ttc_serving_stats;
 int ttc_server_stats(ttc_server* s, ttc_serving_stats* out);
 

@@ -2,6 +2,7 @@
 // host<->device copies, one PRGD iteration (Algorithm 2) as a fixed launch
 // sequence captured once into a CUDA graph per precision, the solver loop
 // and read-back of intermediate results.
+#include <algorithm>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -121,7 +122,8 @@ int drop_graphs(ttc_ctx* c) {
 
 // the fixed launch sequence of one iteration
 int enqueue_iteration(ttc_ctx* c, int prec) {
-  c->hp.bond_fp64 = (prec == TTC_PREC_FP64) ? 1 : 0;   // FP64 steps refine the retraction's SVDs in FP64
+  c->hp.step_fp64 = (prec == TTC_PREC_FP64) ? 1 : 0;
+  c->hp.dense_ff = ttc_dense_ff(c->opt.dense_mode, prec);
   TTC_TRY(ttc_launch_omega_pass(c, prec));
   TTC_TRY(ttc_launch_save_prev(c));   // also the slice weights, which need this step's eps
   TTC_TRY(ttc_launch_dense(c));
@@ -219,6 +221,7 @@ void ttc_default_options(ttc_options* o) {
   o->polish_below = 1e-5;
   o->polish_factor = 10.0;
   o->step_fallback = 1;
+  o->dense_mode = TTC_DENSE_AUTO;
   o->use_graph = 1;
   o->step_rule = TTC_STEP_CONSTANT;
   o->metric = TTC_METRIC_PRECOND;
@@ -260,6 +263,15 @@ int ttc_create(ttc_ctx** out, int d, const int64_t* n, const int32_t* r, const t
     if (r[k] > TTC_MAXR) return TTC_EUNSUPPORTED;
     rmax = r[k] > rmax ? r[k] : rmax;
   }
+  // a TT-rank is at most both dimensions of its unfolding (n_1..n_k rows,
+  // n_{k+1}..n_d columns): no tensor has a larger one, so the manifold of
+  // that rank is empty (products saturate above the largest rank)
+  for (int k = 1; k < d; ++k) {
+    long long left = 1, right = 1;
+    for (int j = 0; j < k; ++j) left = std::min<long long>(left * n[j], 1 << 20);
+    for (int j = k; j < d; ++j) right = std::min<long long>(right * n[j], 1 << 20);
+    if (r[k] > left || r[k] > right) return TTC_EINVAL;
+  }
   ttc_ctx* c = new (std::nothrow) ttc_ctx();
   if (!c) return TTC_ENOMEM;
   ttc_default_options(&c->opt);
@@ -290,7 +302,8 @@ int ttc_create(ttc_ctx** out, int d, const int64_t* n, const int32_t* r, const t
   P.inv_min_n = 1.0 / (double)minn;
   P.inv_2m = 1.0 / (2.0 * (double)d);
   if (c->opt.step_rule < 0 || c->opt.step_rule > 1 || c->opt.metric < 0 || c->opt.metric > 1 ||
-      c->opt.retraction < 0 || c->opt.retraction > 1 || c->opt.precision < 0 || c->opt.precision > 2) {
+      c->opt.retraction < 0 || c->opt.retraction > 1 || c->opt.precision < 0 || c->opt.precision > 2 ||
+      c->opt.dense_mode < 0 || c->opt.dense_mode > 2) {
     delete c;
     return TTC_EINVAL;
   }

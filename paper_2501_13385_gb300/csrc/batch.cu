@@ -169,7 +169,10 @@ int capture(ttc_batch* b) {
     b->exec = nullptr;
   }
   // the retraction refines its SVDs to FP64 accuracy in a member's FP64 steps
-  for (auto* c : b->members) c->hp.bond_fp64 = (c->cur_prec == TTC_PREC_FP64) ? 1 : 0;
+  for (auto* c : b->members) {
+    c->hp.step_fp64 = (c->cur_prec == TTC_PREC_FP64) ? 1 : 0;
+    c->hp.dense_ff = ttc_dense_ff(c->opt.dense_mode, c->cur_prec);
+  }
   TTC_TRY(build_groups(b));
   b->prec_at_capture.clear();
   for (auto* c : b->members) b->prec_at_capture.push_back(c->cur_prec * 2 + c->hp.steepest);

@@ -36,7 +36,8 @@ struct DevProb {
   int steepest;                // step size by exact line search (Eq. (PRGD stepsize))
   int uniform;                 // G_{l,i} = I (RGD)
   int weighted_retraction;     // Remark 3.6: W^{-1/2} SVD^tt_r W^{1/2}
-  int bond_fp64;               // this step's retraction refines its SVDs to FP64 accuracy (FP64 pass)
+  int step_fp64;               // an FP64 step: FP64 pass and FP64 refinement of the retraction's SVDs
+  int dense_ff;                // the block-per-slice dense stages' slice products in float-float (ff.cuh)
 
   // current iterate
   double* core64[TTC_MAXM];    // FP64 master, slice-major, unpadded
@@ -258,7 +259,8 @@ __device__ __forceinline__ void tt_dist_block(const CoresA& A, const CoresB& B, 
 // visible to the whole block; threads stride over the M*N outputs.  The caller
 // synchronises.  op(A) is M x K: A[i*lda + k] or, transposed, A[k*lda + i].
 // The inner sum runs as four independent FMA chains (k mod 4), added at the
-// end: a dependent FP64 FMA costs ~150 cycles on GB300, so one chain per
+// end: in a block of 8 warps a dependent FP64 FMA advances every ~150
+// cycles on GB300 (~1.7 FP64 FMAs per clock per SM), so one chain per
 // output would leave the pipe idle.
 template <typename T>
 __device__ void blk_gemm(int M, int N, int K, const T* A, int lda, bool ta, const T* B, int ldb,

@@ -80,6 +80,12 @@ void ttc_solve_after(ttc_ctx* c, SolveState& st, const double* sc, bool checked)
 bool ttc_solve_needs_metric(const ttc_ctx* c, int it);
 int ttc_read_scalars(ttc_ctx* c, double* out);
 
+// whether a step of pass precision `prec` runs the block-per-slice dense
+// stages' slice products in float-float (TTC_DENSE_*)
+inline int ttc_dense_ff(int mode, int prec) {
+  return (mode == TTC_DENSE_FF || (mode == TTC_DENSE_AUTO && prec != TTC_PREC_FP64)) ? 1 : 0;
+}
+
 // allocation helpers (api.cu): the library's stream-ordered device pool
 cudaError_t ttc_pool_alloc(void** p, size_t bytes, cudaStream_t st);
 void ttc_pool_free(void* p, cudaStream_t st);

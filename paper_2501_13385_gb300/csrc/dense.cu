@@ -32,7 +32,8 @@
 //      so it is left-orthogonal; S_k = P_k^T N_k; the last core is S_{d-2} C_{d-1}.
 //      This is Algorithm 1 itself, not an approximation of it.
 //
-// FP64 on GB300 has a 64-cycle dependent-FMA latency, so every factorization
+// FP64 on GB300 issues ~1.7 FMAs per clock per SM (a dependent FMA of each of
+// a block's 8 warps every ~150 cycles), so every factorization
 // with a long sequential chain runs in FP32 (Cholesky) and is lifted to FP64
 // accuracy by matrix products only (Newton-Schulz for inverses, a second-order
 // correction for the final normalisation).
@@ -53,6 +54,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "ff.cuh"
 #include "linalg.cuh"
 
 namespace {
@@ -88,11 +90,13 @@ __host__ __device__ inline int warp_job_outputs(const Job& J) {
 }
 
 constexpr int kThreads = 256;
+constexpr int kWarpJacobiMax = 16;   // widest bond whose FP32 Jacobi sweeps run on one warp
 
 // y = v^{-1/(2m)} by Newton's iteration for inverse roots,
 // y <- y (1 + (1 - v y^{2m}) / (2m)), started from the FP32 power (relative
 // error ~1e-7); each step squares the error, two steps reach FP64 rounding.
-// (No FP64 pow or division: FP64 has a 64-cycle latency on this GPU.)
+// (No FP64 pow or division: long FP64 chains are slow on this GPU, ~1.7 FP64
+// FMAs per clock per SM.)
 __device__ __forceinline__ double ipow_2m(double y, int two_m) {
   double acc = 1.0, base = y;
   for (int e = two_m; e > 0; e >>= 1) {
@@ -267,7 +271,7 @@ __device__ void post_small_proj(const DevProb& P, double* sm) {
 }
 
 // sum_{t0 <= t < t1} x[t * sx] y[t * sy] with four independent FP64 chains
-// (a dependent FP64 FMA costs ~150 cycles on this GPU)
+// (in a block of 8 warps a dependent FP64 FMA advances every ~150 cycles here)
 __device__ __forceinline__ double dot4(const double* x, int sx, const double* y, int sy, int t0, int t1) {
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
   int t = t0;
@@ -296,14 +300,16 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
   const int q = P.q[k + 1], r = P.r[k + 1];
   const int tid = threadIdx.x, bd = blockDim.x;
   const int qq = q * q;
+  const int ld = q | 1;            // odd leading dimension of the FP32 Jacobi's columns
+  const int qs = q * (q + 1);      // doubles per region
   double* N = sm;                  // q x q, unscaled (the normalisation below)
-  double* RP = N + qq;             // Psi (scaled) -> R_P
-  double* RN = RP + qq;            // N (scaled) -> R_N -> E -> G V (column-major)
-  double* GG = RN + qq;            // G (column-major) -> U, W
-  float* G32 = reinterpret_cast<float*>(GG + qq);   // q x q floats each, column-major (later an FP64 q x q)
-  float* V32 = G32 + qq;
-  double* VD = GG + 2 * qq;        // the FP64 basis V (column-major)
-  double* red = VD + qq;           // blockDim doubles
+  double* RP = N + qs;             // Psi (scaled) -> R_P
+  double* RN = RP + qs;            // N (scaled) -> R_N -> E -> G V (column-major)
+  double* GG = RN + qs;            // G (column-major) -> U, W
+  float* G32 = reinterpret_cast<float*>(GG + qs);   // q x ld floats each, column-major (later an FP64 q x q)
+  float* V32 = G32 + q * ld;
+  double* VD = GG + 2 * qs;        // the FP64 basis V (column-major, leading dimension q)
+  double* red = VD + qs;           // blockDim doubles
   double* dg = red + bd;           // 2q doubles
   __shared__ int bad;
   __shared__ int order[TTC_MAXQ];
@@ -352,15 +358,24 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
     const int j = idx / q, i = idx - j * q;
     const double acc = dot4(RN + i, q, RP + j * q, 1, max(i, j), q);
     GG[idx] = acc;
-    G32[idx] = (float)acc;
-    V32[idx] = (i == j) ? 1.f : 0.f;
+    G32[j * ld + i] = (float)acc;
+    V32[j * ld + i] = (i == j) ? 1.f : 0.f;
     fro = fma(acc, acc, fro);
   }
   fro = blk_sum(fro, red);   // ||G||_F^2: columns below 1e-14 of it (FP32) are zero
-  int sweeps = blk_hestenes<float>(G32, V32, q, 1e-6f, (float)(1e-14 * fro), 24);
-  const bool fp64 = P.bond_fp64 != 0;
+  // FP32 sweeps to 1e-5: the subspace error left (~1e-5 sigma_r sigma_{r+1} /
+  // (sigma_r^2 - sigma_{r+1}^2)) moves the iterate by less than the FP32 pass
+  // does; FP64 steps refine below
+  // up to 16 columns (8 pairs a round, 4 lanes each) one warp runs the
+  // rounds without block barriers; wider bonds need the whole block's lanes
+  int sweeps = q <= kWarpJacobiMax ? warp_hestenes32(G32, V32, q, ld, 1e-5f, (float)(1e-14 * fro), 24)
+                                   : blk_hestenes<float>(G32, V32, q, ld, 1e-5f, (float)(1e-14 * fro), 24);
+  const bool fp64 = P.step_fp64 != 0;
   // the basis in FP64 (converted once: conversions are FP64-pipe work)
-  for (int idx = tid; idx < qq; idx += bd) VD[idx] = (double)V32[idx];
+  for (int idx = tid; idx < qq; idx += bd) {
+    const int j = idx / q, i = idx - j * q;
+    VD[idx] = (double)V32[j * ld + i];
+  }
   if (fp64) {
     // V made orthonormal in FP64, V (I - E/2 + 3 E^2 / 8) with
     // E = V^T V - I (error O(|E|^3)); then FP64 sweeps on G V
@@ -388,7 +403,7 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
       const int j = idx / q, i = idx - j * q;
       RN[idx] = dot4(GG + i, q, VD + j * q, 1, 0, q);
     }
-    sweeps += blk_hestenes<double>(RN, VD, q, 1e-14, 1e-30 * fro, 8);
+    sweeps += blk_hestenes<double>(RN, VD, q, q, 1e-14, 1e-30 * fro, 8);
   }
   __syncthreads();
   // squared singular values (column norms), NaN ordered last
@@ -398,7 +413,7 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
       s2 = dot4(RN + j * q, 1, RN + j * q, 1, 0, q);
     } else {
       float f = 0.f;
-      for (int i = 0; i < q; ++i) f = fmaf(G32[j * q + i], G32[j * q + i], f);
+      for (int i = 0; i < q; ++i) f = fmaf(G32[j * ld + i], G32[j * ld + i], f);
       s2 = f;
     }
     dg[j] = (s2 == s2) ? s2 : -1.0;
@@ -420,7 +435,7 @@ __device__ void post_bond(const DevProb& P, int k, double* sm) {
     U[a * r + c] = dot4(RP + a, q, VD + col * q, 1, 0, a + 1);
   }
   __syncthreads();
-  double* Bm = GG + qq;            // r x r (over G32, V32 and VD, which are not needed any more)
+  double* Bm = GG + qs;            // r x r (over G32, V32 and VD, which are not needed any more)
   double* scr = Bm + r * r;        // 5 r*r
   float* Lf = reinterpret_cast<float*>(scr + 5 * r * r);
   float* Lif = Lf + r * r;
@@ -521,6 +536,226 @@ __device__ void slice_map(const DevProb& P, int k, int x, double* Y) {
   }
 }
 
+// ---- float-float slice products of FP32 steps (block-per-slice path) --------
+// The same sums as slice_contrib and slice_map, on the FP32 pipe (ff.cuh):
+// operands are split into float-float pairs as they are staged in shared
+// memory, transposed where needed so that every product is rows against
+// rows (out(i, j) = sum_t A(i, t) B(j, t)), with odd leading dimensions so
+// that the rows the lanes of a warp read fall in different banks.  The
+// symmetric Grams (Lam, Gam, Psi, N) are accumulated on their upper triangle
+// only and mirrored when the block writes its partial.
+
+constexpr int kFFMaxOut = 9;   // outputs per thread: a 64 x 64 triangle (2080) over 256 threads
+
+__device__ __forceinline__ int ff_ld(int cols) { return cols | 1; }
+
+// dst (rows x cols, leading dimension ld) = split(src), src row-major with
+// leading dimension lds; with `trans` dst is cols x rows: dst[j][i] = src[i][j]
+__device__ void ff_stage(float2* dst, int ld, const double* src, int rows, int cols, int lds, bool trans) {
+  for (int idx = threadIdx.x; idx < rows * cols; idx += blockDim.x) {
+    const int i = idx / cols, j = idx - (idx / cols) * cols;
+    const float2 v = ffa::split(src[i * lds + j]);
+    if (trans)
+      dst[j * ld + i] = v;
+    else
+      dst[i * ld + j] = v;
+  }
+}
+
+// out (M x N, leading dimension ldo) = A (M x K) B^T with B given as N x K
+// rows; results renormalised float-float pairs
+__device__ void ff_mm_rows(int M, int N, int K, const float2* A, int lda, const float2* B, int ldb, float2* out,
+                           int ldo) {
+  for (int idx = threadIdx.x; idx < M * N; idx += blockDim.x) {
+    const int i = idx / N, j = idx - (idx / N) * N;
+    float s, c;
+    ffa::dot(A + i * lda, B + j * ldb, K, s, c);
+    out[i * ldo + j] = ffa::renorm(s, c);
+  }
+}
+
+// this thread's u-th output as i * 65536 + j, or -1: the packed upper
+// triangle (row by row, j >= i) of a rows x rows result when `sym`, else
+// row-major rows x cols
+__device__ __forceinline__ int ff_output(int u, bool sym, int rows, int cols) {
+  int p = threadIdx.x + u * blockDim.x;
+  if (sym) {
+    if (p >= rows * (rows + 1) / 2) return -1;
+    int r = 0;
+    while (p >= rows - r) {
+      p -= rows - r;
+      ++r;
+    }
+    return (r << 16) | (r + p);
+  }
+  if (p >= rows * cols) return -1;
+  return ((p / cols) << 16) | (p - (p / cols) * cols);
+}
+
+// One reduction block of a slice job of an FP32 step: its slices' sum of the
+// job's products, written to the block's partial (rows x cols, mirrored
+// when symmetric) in FP64.
+__device__ void stage_job_ff(const DevProb& P, const Job& J, int b, double* smd) {
+  float2* sm = reinterpret_cast<float2*>(smd);
+  const int k = J.k;
+  const int ra = P.r[k], rb = P.r[k + 1], qa = P.q[k], qb = P.q[k + 1];
+  int qm = 1;
+  for (int t = 0; t <= P.m; ++t) qm = max(qm, P.q[t]);
+  const int reg = qm * (qm + 1);           // float2 per region
+  float2* F = sm;                          // the fixed matrix of the job
+  float2* X = F + reg;                     // the slice's operand
+  float2* Y = X + reg;                     // the first product
+  float2* X2 = Y + reg;                    // a second slice operand (E of OP_H)
+  const bool sym = J.op != OP_H;
+  float as[kFFMaxOut], ac[kFFMaxOut];
+  int oij[kFFMaxOut];
+#pragma unroll
+  for (int u = 0; u < kFFMaxOut; ++u) {
+    as[u] = ac[u] = 0.f;
+    oij[u] = ff_output(u, sym, J.rows, J.cols);
+  }
+  // the fixed matrix (the same for every slice)
+  int ldF = 1;
+  switch (J.op) {
+    case OP_LAM: ldF = ff_ld(ra); ff_stage(F, ldF, P.small + P.off_lam[k], ra, ra, ra, false); break;
+    case OP_GAM: ldF = ff_ld(rb); ff_stage(F, ldF, P.small + P.off_gam[k + 1], rb, rb, rb, false); break;
+    case OP_PSI: ldF = ff_ld(qb); ff_stage(F, ldF, P.small + P.off_psi[k + 1], qb, qb, qb, false); break;
+    case OP_N:
+      if (k > 0) {
+        ldF = ff_ld(qa);
+        ff_stage(F, ldF, P.small + P.off_sk[k - 1], ra, qa, qa, false);
+      }
+      break;
+    default: break;
+  }
+  for (int x = b; x < P.n[k]; x += J.nb) {
+    __syncthreads();   // the previous slice's reads are done (and F is staged)
+    const double* T = P.core64[k] + (long long)x * ra * rb;
+    const double* C = P.C[k] + (long long)x * qa * qb;
+    const float2 *L = nullptr, *R = nullptr;   // the second product: out(i, j) = sum_t L(i, t) R(j, t)
+    int ldL = 1, ldR = 1, K = 0;
+    float2 w = make_float2(1.f, 0.f);
+    switch (J.op) {
+      case OP_LAM: {   // acc += w T^T (Lam T): Y^T = T^T Lam (Lam symmetric), out = w T^T Y
+        const int ldX = ff_ld(ra);
+        ff_stage(X, ldX, T, ra, rb, rb, true);                 // T^T: rb x ra
+        __syncthreads();
+        ff_mm_rows(rb, ra, ra, X, ldX, F, ldF, Y, ldX);         // Y^T: rb x ra
+        L = X; ldL = ldX; R = Y; ldR = ldX; K = ra;
+        w = ffa::split(gpow(P, k, x, +1));
+        break;
+      }
+      case OP_GAM: {   // acc += w (T Gam) T^T: Y = T Gam, out = w Y T^T
+        const int ldX = ff_ld(rb);
+        ff_stage(X, ldX, T, ra, rb, rb, false);                // T: ra x rb
+        __syncthreads();
+        ff_mm_rows(ra, rb, rb, X, ldX, F, ldF, Y, ldX);         // Y: ra x rb
+        L = Y; ldL = ldX; R = X; ldR = ldX; K = rb;
+        w = ffa::split(gpow(P, k, x, +1));
+        break;
+      }
+      case OP_H: {     // acc += T^T E
+        const int ldX = ff_ld(ra);
+        ff_stage(X, ldX, T, ra, rb, rb, true);                 // T^T: rb x ra
+        ff_stage(X2, ldX, P.E[k] + (long long)x * ra * rb, ra, rb, rb, true);
+        L = X; ldL = ldX; R = X2; ldR = ldX; K = ra;
+        break;
+      }
+      case OP_PSI: {   // acc += (C Psi) C^T: Y = C Psi (Psi symmetric), out = Y C^T
+        const int ldX = ff_ld(qb);
+        ff_stage(X, ldX, C, qa, qb, qb, false);                // C: qa x qb
+        __syncthreads();
+        ff_mm_rows(qa, qb, qb, X, ldX, F, ldF, Y, ldX);         // Y: qa x qb
+        L = Y; ldL = ldX; R = X; ldR = ldX; K = qb;
+        break;
+      }
+      default: {       // OP_N: C' = S_{k-1} C, acc += C'^T C'
+        const int ldX = ff_ld(qa);
+        ff_stage(X, ldX, C, qa, qb, qb, true);                 // C^T: qb x qa
+        if (k == 0) {
+          L = X; ldL = ldX; R = X; ldR = ldX; K = qa;
+        } else {
+          __syncthreads();
+          const int ldY = ff_ld(ra);
+          ff_mm_rows(qb, ra, qa, X, ldX, F, ldF, Y, ldY);       // C'^T: qb x ra
+          L = Y; ldL = ldY; R = Y; ldR = ldY; K = ra;
+        }
+        break;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kFFMaxOut; ++u) {
+      if (oij[u] >= 0) {
+        const int i = oij[u] >> 16, j = oij[u] & 0xffff;
+        float s, c;
+        ffa::dot(L + i * ldL, R + j * ldR, K, s, c);
+        ffa::acc_scaled(as[u], ac[u], w, s, c);
+      }
+    }
+  }
+  const int dd = J.rows * J.cols;
+  double* out = P.red + J.red + (long long)b * dd;
+#pragma unroll
+  for (int u = 0; u < kFFMaxOut; ++u) {
+    if (oij[u] >= 0) {
+      const int i = oij[u] >> 16, j = oij[u] & 0xffff;
+      const double v = ffa::join(as[u], ac[u]);
+      out[i * J.cols + j] = v;
+      if (sym) out[j * J.cols + i] = v;
+    }
+  }
+}
+
+// new core k at slice x in an FP32 step (the sums of slice_map in float-float)
+__device__ void slice_map_ff(const DevProb& P, int k, int x, double* smd) {
+  float2* sm = reinterpret_cast<float2*>(smd);
+  const int m = P.m;
+  const int qa = P.q[k], qb = P.q[k + 1];
+  const int ra = P.r[k], rb = P.r[k + 1];
+  int qm = 1;
+  for (int t = 0; t <= m; ++t) qm = max(qm, P.q[t]);
+  const int reg = qm * (qm + 1);
+  float2* Sf = sm;                 // S_{k-1}: ra x qa
+  float2* Ct = Sf + reg;           // C^T: qb x qa
+  float2* Cp = Ct + reg;           // C' = S_{k-1} C: ra x qb
+  float2* Pt = Cp + reg;           // P_k^T: rb x qb
+  const double* C = P.C[k] + (long long)x * qa * qb;
+  const int ldC = ff_ld(qb);
+  if (k > 0) {
+    const int ldS = ff_ld(qa);
+    ff_stage(Sf, ldS, P.small + P.off_sk[k - 1], ra, qa, qa, false);
+    ff_stage(Ct, ldS, C, qa, qb, qb, true);
+    __syncthreads();
+    ff_mm_rows(ra, qb, qa, Sf, ldS, Ct, ldS, Cp, ldC);
+  } else {
+    ff_stage(Cp, ldC, C, qa, qb, qb, false);   // C' = C (qa = ra = 1)
+  }
+  if (k < m - 1) ff_stage(Pt, ldC, P.small + P.off_pk[k], qb, rb, rb, true);
+  __syncthreads();
+  // Remark 3.6: the rounding ran on W^{1/2} W_l; undo the weight
+  const double wu = P.weighted_retraction ? sqrt(gpow(P, k, x, -1)) : 1.0;
+  double* T = P.core64[k] + (long long)x * ra * rb;
+  float* T32 = P.core32p[k] + (long long)x * P.R * P.R;
+  double* T64 = P.core64p[k] + (long long)x * P.R * P.R;
+  for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
+    const int a = i / rb, bcol = i - (i / rb) * rb;
+    double v;
+    if (k < m - 1) {
+      float s, c;
+      ffa::dot(Cp + a * ldC, Pt + bcol * ldC, qb, s, c);
+      v = ffa::join(s, c);
+    } else {
+      const float2 e = Cp[a * ldC + bcol];
+      v = ffa::join(e.x, e.y);
+    }
+    if (P.weighted_retraction) v *= wu;
+    T[i] = v;
+    T32[pad_idx(P, k, a, bcol)] = (float)v;
+    T64[pad_idx(P, k, a, bcol)] = v;
+  }
+}
+
 // Sums n partial rows of d values (src + row * d) into dst[0..d) in a fixed
 // order: G = blockDim / d thread groups split the rows, each thread keeps
 // four independent register accumulators (loads pipeline, FP64 adds
@@ -612,7 +847,10 @@ __global__ void __launch_bounds__(kThreads) k_stage(const DevProb P, const Stage
   for (int i = 0; i < S.nmap; ++i) {     // slice maps first
     const int k = S.map_k[i];
     if (b < P.n[k]) {
-      slice_map(P, k, b, sm);
+      if (P.dense_ff)
+        slice_map_ff(P, k, b, sm);
+      else
+        slice_map(P, k, b, sm);
       return;
     }
     b -= P.n[k];
@@ -623,14 +861,18 @@ __global__ void __launch_bounds__(kThreads) k_stage(const DevProb P, const Stage
     ++j;
   }
   const Job J = S.job[j];
-  const int dd = J.rows * J.cols;
-  double* acc = sm;
-  double* Y = sm + dd;
-  for (int i = threadIdx.x; i < dd; i += blockDim.x) acc[i] = 0.0;
-  __syncthreads();
-  for (int x = b; x < P.n[J.k]; x += J.nb) slice_contrib(P, S, J, x, acc, Y);
-  double* out = P.red + J.red + (long long)b * dd;
-  for (int i = threadIdx.x; i < dd; i += blockDim.x) out[i] = acc[i];
+  if (P.dense_ff && J.op <= OP_N) {
+    stage_job_ff(P, J, b, sm);           // the slice products in float-float
+  } else {
+    const int dd = J.rows * J.cols;
+    double* acc = sm;
+    double* Y = sm + dd;
+    for (int i = threadIdx.x; i < dd; i += blockDim.x) acc[i] = 0.0;
+    __syncthreads();
+    for (int x = b; x < P.n[J.k]; x += J.nb) slice_contrib(P, S, J, x, acc, Y);
+    double* out = P.red + J.red + (long long)b * dd;
+    for (int i = threadIdx.x; i < dd; i += blockDim.x) out[i] = acc[i];
+  }
   if (!stage_reduce(P, S, j, b, sm)) return;   // the stage's last group finisher continues
   if (S.post == POST_SMALL_PROJ) {
     post_small_proj(P, sm);
@@ -675,7 +917,7 @@ __device__ __forceinline__ void warp_mm_t(double* Y, const double* X, int ldx, c
   const int lane = threadIdx.x & 31;
   for (int e = lane; e < M * N; e += 32) {
     const int i = e / N, j = e - (e / N) * N;
-    double a0 = 0.0, a1 = 0.0;   // two chains: a dependent FP64 FMA costs ~150 cycles
+    double a0 = 0.0, a1 = 0.0;   // two chains: FP64 chains advance slowly here
     int t = 0;
     for (; t + 1 < K; t += 2) {
       a0 = fma(X[i * ldx + t], Z[t * ldz + j], a0);
@@ -1594,10 +1836,12 @@ int ttc_alloc_dense(ttc_ctx* c) {
   size_t red_need = sizeof(double) * (size_t)(2 * qmax * qmax);
   red_need = std::max(red_need, sizeof(double) * (size_t)(2 * TTC_MAXR * TTC_MAXR));
   size_t proj_need = sizeof(double) * (size_t)(8 * 2 * rmax * rmax) + sizeof(float) * (size_t)(8 * 2 * rmax * rmax);
-  // the bond: N, the two factors, G, the FP32 pair G32 / V32, the FP64 basis (6 q^2 doubles), the
-  // block's reduction slots and the factor diagonals
-  size_t bond_need = sizeof(double) * (size_t)(6 * qmax * qmax + kThreads + 2 * qmax);
-  pl.smem_stage = std::max(red_need, std::max(proj_need, bond_need)) + 64;
+  // the bond: N, the two factors, G, the FP32 pair G32 / V32, the FP64 basis (6 regions of
+  // q (q + 1) doubles), the block's reduction slots and the factor diagonals
+  size_t bond_need = sizeof(double) * (size_t)(6 * qmax * (qmax + 1) + kThreads + 2 * qmax);
+  // float-float slice jobs and maps of FP32 steps: four regions of q (q + 1) float pairs
+  size_t ff_need = sizeof(float2) * (size_t)(4 * qmax * (qmax + 1));
+  pl.smem_stage = std::max(std::max(red_need, ff_need), std::max(proj_need, bond_need)) + 64;
   pl.smem_warp = pl.warp ? std::max(pl.smem_stage, sizeof(double) * (size_t)kWarpsW * 3 * wscr_mat_host(P))
                          : pl.smem_stage;
   {
@@ -1675,7 +1919,7 @@ int ttc_launch_dense(ttc_ctx* c) {
     k_build_B1<<<nslices, 128, 0, st>>>(P);
     TTC_CUDA(cudaGetLastError());
     const int tb = tangent_blocks(P);
-    if (P.bond_fp64) {   // an FP64 step: ||P_Omega Z||^2 in FP64
+    if (P.step_fp64) {   // an FP64 step: ||P_Omega Z||^2 in FP64
       TTC_TRY(launch_tangent<double>(c, tb, nslices, st));
     } else {
       TTC_TRY(launch_tangent<float>(c, tb, nslices, st));

@@ -79,8 +79,9 @@ static __device__ int blk_spd_inverse(double* A, int n, double* work, int* flag)
 }
 
 // ---------------------------------------------------------------------------
-// Warp-level helpers for the small factorizations.  GB300's FP64 pipe has a
-// 64-cycle dependent-FMA latency, so factorizations with long sequential
+// Warp-level helpers for the small factorizations.  GB300's FP64 pipe issues
+// ~1.7 FMAs per clock per SM (a block's 8 warps each advance a dependent
+// FP64 chain every ~150 cycles), so factorizations with long sequential
 // chains (Cholesky pivots, Jacobi rotations) run in FP32 and are brought to
 // FP64 accuracy by refinement steps that are matrix products only.
 // ---------------------------------------------------------------------------
@@ -143,8 +144,8 @@ static __device__ int warp_chol_inv32(const double* A, int lda, int n, float* L,
 }
 
 // C (M x N, ldc) = alpha op(A) op(B) (+ C when accumulate) by one warp.  Four
-// independent FMA chains per output (k mod 4): a dependent FP64 FMA costs
-// ~150 cycles on this GPU.
+// independent FMA chains per output (k mod 4): FP64 chains advance slowly
+// on this GPU (~1.7 FP64 FMAs per clock per SM).
 template <typename T>
 __device__ void warp_gemm(int M, int N, int K, const T* A, int lda, bool ta, const T* B, int ldb, bool tb, T* C,
                           int ldc, T alpha, bool accumulate) {
@@ -321,7 +322,7 @@ static __device__ void blk_chol2_upper_psd(double* A, double* B, int n, double* 
 }
 
 // One-sided (Hestenes) Jacobi: plane rotations of the columns of G (n x n,
-// n <= 64, column-major: column j at G + j*n) until they are mutually
+// n <= 64, column-major: column j at G + j*ld, the same for V) until they are mutually
 // orthogonal, so that G V = U diag(sigma), with the rotations accumulated in
 // V (column-major, enter with the starting basis).  A sweep is the
 // round-robin ordering: n' - 1 rounds (n' = n rounded up to even) of n'/2
@@ -340,7 +341,7 @@ static __device__ void blk_chol2_upper_psd(double* A, double* B, int n, double* 
 // rotations act on the factor, not on its Gram, so singular values of very
 // different sizes keep their relative accuracy.
 template <typename T>
-static __device__ int blk_hestenes(T* G, T* V, int n, T tol, T floor, int max_sweeps) {
+static __device__ int blk_hestenes(T* G, T* V, int n, int ld, T tol, T floor, int max_sweeps) {
   const int lp = n <= 16 ? 4 : 8;
   const int lane = threadIdx.x & 31;
   const int slot = (threadIdx.x >> 5) * (32 / lp) + lane / lp;
@@ -379,8 +380,8 @@ static __device__ int blk_hestenes(T* G, T* V, int n, T tol, T floor, int max_sw
 #pragma unroll
         for (int h = 0; h < MR; ++h) {
           const int row = sub + h * lp;
-          ca[h] = (act && row < n) ? G[p * n + row] : T(0);
-          cb[h] = (act && row < n) ? G[q * n + row] : T(0);
+          ca[h] = (act && row < n) ? G[p * ld + row] : T(0);
+          cb[h] = (act && row < n) ? G[q * ld + row] : T(0);
           al = fma(ca[h], ca[h], al);
           be = fma(cb[h], cb[h], be);
           ga = fma(ca[h], cb[h], ga);
@@ -392,32 +393,52 @@ static __device__ int blk_hestenes(T* G, T* V, int n, T tol, T floor, int max_sw
         }
         // a column below the floor is zero to the working precision: its
         // direction is noise and never settles, so it is not rotated
-        if (act && fmin(al, be) > floor && fabs(ga) > tol * sqrt(al * be)) {
+        if (act && fmin(al, be) > floor && ga * ga > tol * tol * (al * be)) {
           T tt, cs;
+          // the angle needs no correct rounding: a rotation by a slightly
+          // different angle is still orthogonal, and the next sweep removes
+          // what it leaves; so it is found in FP32 with fast reciprocals
+          // (FP64 from FP64 sums: b - a in FP64 first; a chain of FP64
+          // divisions and square roots is slow on this GPU)
+          float zn, zd;
           if constexpr (sizeof(T) == 4) {
-            // FP32 sweeps: the angle needs no correct rounding (a rotation
-            // by a slightly different angle is still orthogonal and the
-            // next sweep removes what it leaves), so fast reciprocals
-            const float z = __fdividef(be - al, 2.f * ga);
-            const float az = fabsf(z);
-            tt = az > 1e15f ? __fdividef(0.5f, z) : copysignf(__frcp_rn(az + sqrtf(fmaf(z, z, 1.f))), z);
+            zn = be - al;
+            zd = 2.f * ga;
+          } else {
+            // scaled by a power of two (exact) that brings |ga| into [1, 2):
+            // sums of tiny columns would underflow FP32
+            const int eg = (__double2hiint(ga) >> 20) & 0x7ff;
+            const double sc = __hiloint2double((2046 - eg) << 20, 0);
+            zn = (float)fmin(fmax((be - al) * sc, -1e30), 1e30);
+            zd = 2.f * (float)(ga * sc);
+          }
+          const float z = __fdividef(zn, zd);
+          const float az = fabsf(z);
+          const float tf = az > 1e15f ? __fdividef(0.5f, z) : copysignf(__frcp_rn(az + sqrtf(fmaf(z, z, 1.f))), z);
+          if constexpr (sizeof(T) == 4) {
+            tt = tf;
             cs = rsqrtf(fmaf(tt, tt, 1.f));
           } else {
-            const T z = (be - al) / (T(2) * ga);
-            const T az = fabs(z);
-            tt = az > T(1e15) ? T(0.5) / z : copysign(T(1), z) / (az + sqrt(fma(z, z, T(1))));
-            cs = rsqrt(fma(tt, tt, T(1)));
+            // cs = 1 / sqrt(1 + t^2) to FP64 accuracy for the t used, so that
+            // cs^2 + sn^2 = 1 and the rotation stays orthogonal: Newton's
+            // iteration for the inverse square root, y <- y (3 - x y^2) / 2,
+            // from the FP32 value (relative error ~2^-22 -> ~1e-13 -> FP64)
+            tt = (double)tf;
+            const double x = fma(tt, tt, 1.0);
+            double y = (double)rsqrtf((float)x);
+            for (int it = 0; it < 2; ++it) y = fma(y, fma(-0.5 * x, y * y, 0.5), y);
+            cs = y;
           }
           const T sn = cs * tt;
 #pragma unroll
           for (int h = 0; h < MR; ++h) {
             const int row = sub + h * lp;
             if (row < n) {
-              G[p * n + row] = fma(cs, ca[h], -sn * cb[h]);
-              G[q * n + row] = fma(sn, ca[h], cs * cb[h]);
-              const T x = V[p * n + row], y = V[q * n + row];
-              V[p * n + row] = fma(cs, x, -sn * y);
-              V[q * n + row] = fma(sn, x, cs * y);
+              G[p * ld + row] = fma(cs, ca[h], -sn * cb[h]);
+              G[q * ld + row] = fma(sn, ca[h], cs * cb[h]);
+              const T x = V[p * ld + row], y = V[q * ld + row];
+              V[p * ld + row] = fma(cs, x, -sn * y);
+              V[q * ld + row] = fma(sn, x, cs * y);
             }
           }
           mine = 1;
@@ -429,4 +450,99 @@ static __device__ int blk_hestenes(T* G, T* V, int n, T tol, T floor, int max_sw
     if (!__syncthreads_or(mine)) break;
   }
   return sweep;
+}
+
+// One-sided Jacobi in FP32 by a single warp (the other warps of the block wait
+// at the closing barrier): column-major G and V with an odd leading dimension
+// ld >= n, so that the columns the lanes of a round read at the same row sit
+// in different banks.  The n'/2 pairs of a round (n' = n rounded up to even)
+// are spread over the 32 lanes, lp lanes per pair (8, 4, 2 or 1 as n'/2 is
+// at most 4, 8, 16 or 32), each lane owning every lp-th row; rounds are
+// separated by __syncwarp only, so a round costs the dependent arithmetic of
+// one pair (the block-wide form pays a block barrier and idle warps per
+// round).  Pair (p, q) is rotated as in blk_hestenes; columns at or below
+// `floor` are not rotated.  Returns the sweeps run.
+static __device__ int warp_hestenes32(float* G, float* V, int n, int ld, float tol, float floor, int max_sweeps) {
+  __shared__ unsigned char wpairs[2 * 63 * 32];
+  __shared__ int wsweeps;
+  const int n2 = n + (n & 1), np = n2 / 2;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < (n2 - 1) * np; idx += blockDim.x) {
+    const int t = idx / np, i = idx - t * np;
+    const int pa = (i == 0) ? 0 : ((i - 1 + t) % (n2 - 1)) + 1;
+    const int pb = ((n2 - 2 - i + t) % (n2 - 1)) + 1;
+    wpairs[2 * idx] = (unsigned char)min(pa, pb);
+    wpairs[2 * idx + 1] = (unsigned char)max(pa, pb);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lp = np <= 4 ? 8 : np <= 8 ? 4 : np <= 16 ? 2 : 1;
+    const int lane = threadIdx.x, slot = lane / lp, sub = lane - slot * lp;
+    int sweep = 0;
+    while (sweep < max_sweeps) {
+      int mine = 0;
+      for (int t = 0; t < n2 - 1; ++t) {
+        int p = 0, q = 0;
+        bool act = false;
+        if (slot < np) {
+          p = wpairs[2 * (t * np + slot)];
+          q = wpairs[2 * (t * np + slot) + 1];
+          act = q < n;   // not the dummy column of an odd n
+        }
+        const float* gp = G + p * ld;
+        const float* gq = G + q * ld;
+        float al0 = 0.f, be0 = 0.f, ga0 = 0.f, al1 = 0.f, be1 = 0.f, ga1 = 0.f;
+        if (act) {
+          int row = sub;
+          for (; row + lp < n; row += 2 * lp) {
+            const float a0 = gp[row], b0 = gq[row], a1 = gp[row + lp], b1 = gq[row + lp];
+            al0 = fmaf(a0, a0, al0);
+            be0 = fmaf(b0, b0, be0);
+            ga0 = fmaf(a0, b0, ga0);
+            al1 = fmaf(a1, a1, al1);
+            be1 = fmaf(b1, b1, be1);
+            ga1 = fmaf(a1, b1, ga1);
+          }
+          if (row < n) {
+            const float a0 = gp[row], b0 = gq[row];
+            al0 = fmaf(a0, a0, al0);
+            be0 = fmaf(b0, b0, be0);
+            ga0 = fmaf(a0, b0, ga0);
+          }
+        }
+        float al = al0 + al1, be = be0 + be1, ga = ga0 + ga1;
+        for (int o = lp / 2; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (act && fminf(al, be) > floor && ga * ga > tol * tol * (al * be)) {
+          // the angle needs no correct rounding: fast reciprocals
+          const float z = __fdividef(be - al, 2.f * ga);
+          const float az = fabsf(z);
+          const float tt = az > 1e15f ? __fdividef(0.5f, z) : copysignf(__frcp_rn(az + sqrtf(fmaf(z, z, 1.f))), z);
+          const float cs = rsqrtf(fmaf(tt, tt, 1.f)), sn = cs * tt;
+          float* wp = G + p * ld;
+          float* wq = G + q * ld;
+          float* vp = V + p * ld;
+          float* vq = V + q * ld;
+          for (int row = sub; row < n; row += lp) {
+            const float a = wp[row], b = wq[row];
+            wp[row] = fmaf(cs, a, -sn * b);
+            wq[row] = fmaf(sn, a, cs * b);
+            const float x = vp[row], y = vq[row];
+            vp[row] = fmaf(cs, x, -sn * y);
+            vq[row] = fmaf(sn, x, cs * y);
+          }
+          mine = 1;
+        }
+        __syncwarp();
+      }
+      ++sweep;
+      if (!__any_sync(0xffffffffu, mine)) break;
+    }
+    if (lane == 0) wsweeps = sweep;
+  }
+  __syncthreads();
+  return wsweeps;
 }

@@ -823,10 +823,14 @@ __device__ __forceinline__ void sample_project(const DevProb& P, const int blk) 
 
 // resident blocks per SM the register budget is sized for: FP32 first/last
 // modes (one gather per entry, r accumulators) keep four 256-thread blocks,
-// small FP32 interior ranks two (16 warps, two gathers in flight each)
+// small FP32 interior ranks two (16 warps, two gathers in flight each), and
+// so do FP32 interior ranks up to 24 (the block-per-chunk form: 128
+// registers instead of the 160 it takes unbounded, which left one block of
+// 8 warps per SM to hide the row gathers)
 template <typename T, int RC, int MC>
 constexpr int min_blocks() {
-  return sizeof(T) != 4 || RC > 8 ? 1
+  return sizeof(T) != 4 ? 1
+         : RC > 8 ? ((MC == PC_MIDDLE && RC <= 24) ? 2 : 1)
          : (MC == PC_FIRST || MC == PC_LAST) ? (RC <= 6 ? 4 : 3)
          : (MC == PC_MIDDLE && RC <= 5) ? 2 : 1;
 }

@@ -92,6 +92,9 @@ struct ttc_server {
   long long iterations = 0;
   long long launches = 0;     // kernels launched by the engine's ticks
   double busy_ms = 0.0;
+  long long rebuilds = 0;     // batch (re)captures
+  double rebuild_ms = 0.0;    // engine time spent in them
+  double admit_ms = 0.0;      // engine time spent admitting requests
   Clock::time_point t0;
 };
 
@@ -219,7 +222,12 @@ void engine_loop(ttc_server* S) {
         S->used += rq->est_bytes;
       }
       Slot sl;
+      const auto ta = Clock::now();
       int s = admit(S, rq, sl);
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->admit_ms += ms_between(ta, Clock::now());
+      }
       if (s != TTC_OK) {
         finish(S, sl, s);
         continue;
@@ -235,7 +243,13 @@ void engine_loop(ttc_server* S) {
       S->batch = nullptr;
       std::vector<ttc_ctx*> members;
       for (auto& sl : S->slots) members.push_back(sl.ctx);
+      const auto tb = Clock::now();
       int s = ttc_batch_create(&S->batch, members.data(), (int)members.size(), S->stream);
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->rebuilds += 1;
+        S->rebuild_ms += ms_between(tb, Clock::now());
+      }
       if (s != TTC_OK) {
         for (auto& sl : S->slots) finish(S, sl, s);
         S->slots.clear();
@@ -443,6 +457,9 @@ int ttc_server_stats(ttc_server* S, ttc_serving_stats* out) {
   out->launches = S->launches;
   out->entry_iterations = S->entry_iters;
   out->busy_ms = S->busy_ms;
+  out->rebuilds = S->rebuilds;
+  out->rebuild_ms = S->rebuild_ms;
+  out->admit_ms = S->admit_ms;
   out->wall_ms = ms_between(S->t0, Clock::now());
   out->p50_ms = out->p99_ms = out->max_ms = 0.0;
   if (!S->latencies.empty()) {

@@ -20,6 +20,7 @@ STOP_RELERR, STOP_STEP, STOP_NONE, STOP_RESID = 0, 1, 2, 3
 STEP_CONSTANT, STEP_STEEPEST = 0, 1
 METRIC_PRECOND, METRIC_UNIFORM = 0, 1
 RETRACT_PLAIN, RETRACT_WEIGHTED = 0, 1
+DENSE_AUTO, DENSE_FP64, DENSE_FF = 0, 1, 2
 
 STATUS = {
     0: "TTC_OK", -1: "TTC_EINVAL", -2: "TTC_ENOMEM", -3: "TTC_ERANGE", -4: "TTC_EDUP",
@@ -43,7 +44,7 @@ class Options(C.Structure):
         ("eps_frozen", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int), ("stop_rule", C.c_int),
         ("check_every", C.c_int), ("polish_below", C.c_double), ("use_graph", C.c_int),
         ("step_rule", C.c_int), ("metric", C.c_int), ("retraction", C.c_int), ("polish_factor", C.c_double),
-        ("step_fallback", C.c_int),
+        ("step_fallback", C.c_int), ("dense_mode", C.c_int),
     ]
 
 
@@ -76,7 +77,8 @@ class ServingStats(C.Structure):
     _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("queued", C.c_int64),
                 ("iterations", C.c_int64), ("launches", C.c_int64), ("entry_iterations", C.c_double),
                 ("busy_ms", C.c_double), ("wall_ms", C.c_double), ("p50_ms", C.c_double),
-                ("p99_ms", C.c_double), ("max_ms", C.c_double)]
+                ("p99_ms", C.c_double), ("max_ms", C.c_double), ("rebuilds", C.c_int64),
+                ("rebuild_ms", C.c_double), ("admit_ms", C.c_double)]
 
 
 _lib = None

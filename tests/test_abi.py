@@ -49,6 +49,26 @@ def test_default_options_from_library(built_lib):
     o = ttc.default_options()
     assert o.precision == ttc.PREC_MIXED and o.eps_rel == 1.0 and o.alpha_scale == 1.5
     assert o.max_iter == 500 and o.use_graph == 1
+    assert o.step_fallback == 1 and o.dense_mode == ttc.DENSE_AUTO and o.polish_factor == 10.0
+
+
+@pytest.mark.parametrize("n,r", [
+    ([12, 10, 11, 9], [1, 12, 17, 11, 1]),    # r_3 = 11 > n_4 = 9
+    ([3, 40, 40], [1, 4, 2, 1]),              # r_1 = 4 > n_1 = 3
+    ([2, 2, 2, 2], [1, 2, 5, 2, 1]),          # r_2 = 5 > n_1 n_2 = 4
+])
+def test_infeasible_tt_ranks_are_rejected_before_any_device_work(built_lib, n, r):
+    # a TT-rank above either dimension of its unfolding is no tensor's rank;
+    # ttc_create refuses it before it touches the GPU (so this runs here)
+    from paper_2501_13385_gb300 import ttc
+    import numpy as np
+    L = ttc.lib()
+    h = ctypes.c_void_p()
+    na = np.asarray(n, dtype=np.int64)
+    ra = np.asarray(r, dtype=np.int32)
+    st = L.ttc_create(ctypes.byref(h), len(n), na.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                      ra.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), None, None)
+    assert st == -1 and not h.value
 
 
 def test_compiled_for_sm_103a_only():

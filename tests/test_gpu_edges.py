@@ -64,3 +64,48 @@ def test_empty_and_oversized_inputs_are_rejected():
         ttc.Context([1 << 17] * 7, [1] + [2] * 6 + [1]).set_observations(
             np.zeros((1, 7), dtype=np.int32), np.zeros(1))
     assert e.value.status in (-10, -1)
+
+
+@pytest.mark.parametrize("spec", [
+    dict(n=[30, 28, 26], r=[1, 9, 10, 1], count=15000),
+    dict(n=[40, 40, 40], r=[1, 20, 20, 1], count=48000),
+    dict(n=[12, 10, 11, 13], r=[1, 12, 17, 11, 1], count=9000),
+    dict(n=[64, 64, 64], r=[1, 32, 32, 1], count=100000),
+], ids=lambda s: "r" + "-".join(map(str, s["r"][1:-1])))
+def test_float_float_dense_stages_match_oracle(spec):
+    # FP64 steps whose slice products (the Grams and the new cores) run in
+    # float-float, as every FP32 step's do: the products are accurate to
+    # ~1e-11 relative to sum |a_i b_i| (compensated dot products of 48-bit
+    # operands), so the step stays within 1e-8 of the oracle's (an FP32
+    # product would miss by ~1e-6, a wrong index by O(1)); two steps, so
+    # that the second starts from iterates the float-float path made
+    P = w.random_problem(78, spec["n"], spec["r"], spec["count"], init_rel=0.1)
+    cur = P.init
+    with ttc.Context(P.n, P.r, precision=ttc.PREC_FP64, dense_mode=ttc.DENSE_FF) as c:
+        c.set_observations(P.idx, P.y)
+        c.set_cores(P.init)
+        for _ in range(2):
+            c.step()
+            cur, _ = o.prgd_step(cur, P.idx, P.y, P.n, P.r, eps_rel=1.0, alpha_scale=1.5)
+            assert o.tt_dist(c.get_cores(), cur) <= 1e-8 * o.tt_norm(cur)
+
+
+def test_dense_mode_fp64_keeps_fp32_steps_in_fp64():
+    # TTC_DENSE_FP64: an FP32 step's slice products in FP64; the step still
+    # carries the FP32 pass's error, so it is compared within 2e-5 (as the
+    # mixed steps of the full-size tests), and against the default
+    # (float-float) FP32 step, which must agree to the same bound
+    P = w.random_problem(79, [40, 40, 40], [1, 20, 20, 1], 48000, init_rel=0.1)
+    ref, _ = o.prgd_step(P.init, P.idx, P.y, P.n, P.r, eps_rel=1.0, alpha_scale=1.5)
+    got = {}
+    for mode in (ttc.DENSE_FP64, ttc.DENSE_AUTO):
+        with ttc.Context(P.n, P.r, precision=ttc.PREC_FP32, dense_mode=mode) as c:
+            c.set_observations(P.idx, P.y)
+            c.set_cores(P.init)
+            c.step()
+            got[mode] = c.get_cores()
+        assert o.tt_dist(got[mode], ref) <= 2e-5 * o.tt_norm(ref)
+    assert o.tt_dist(got[ttc.DENSE_FP64], got[ttc.DENSE_AUTO]) <= 2e-5 * o.tt_norm(ref)
+    with pytest.raises(ttc.TTCError) as e:
+        ttc.Context(P.n, P.r, dense_mode=3)
+    assert e.value.status == -1

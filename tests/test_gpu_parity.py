@@ -258,12 +258,14 @@ def test_full_size_sampled_slices(maker):
 
 
 def test_diverging_solve_never_reports_convergence():
-    # an absurd step scale makes the iteration diverge: the solver must end
-    # with TTC_ENOTCONV or TTC_ENONFINITE (a non-finite metric is never read
-    # as converged), whichever comes first
+    # an absurd step scale, with the divergence fallback off, makes the
+    # iteration diverge: the solver must end with TTC_ENOTCONV or
+    # TTC_ENONFINITE (a non-finite metric is never read as converged),
+    # whichever comes first
     P = w.planted_small(6)
     for rule in (ttc.STOP_RELERR, ttc.STOP_STEP):
-        with ctx_for(P, precision=ttc.PREC_FP64, alpha_scale=1e4, stop_rule=rule, tol=1e-6, max_iter=200) as c:
+        with ctx_for(P, precision=ttc.PREC_FP64, alpha_scale=1e4, step_fallback=0, stop_rule=rule, tol=1e-6,
+                     max_iter=200) as c:
             c.set_truth(P.truth)
             try:
                 res = c.solve()

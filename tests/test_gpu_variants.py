@@ -137,3 +137,69 @@ def test_qst_workload_mixed_solve_converges():
         c.set_truth(P.truth)
         res = c.solve()
         assert res["converged"], res
+
+
+def _oracle_with_fallback(P, alpha_scale, iters):
+    """The oracle's iterates under the divergence fallback: constant steps of
+    Theorem 4.1's form until the relative residual more than doubles from one
+    iteration to the next, the steepest step of Eq. (PRGD stepsize) from the
+    following iteration on.  Returns (cores, the first steepest iteration or
+    -1)."""
+    yn = np.linalg.norm(P.y)
+    cur, prev, steep, fb = P.init, -1.0, False, -1
+    for it in range(1, iters + 1):
+        rel = float(np.linalg.norm(o.residual(cur, P.idx, P.y))) / yn
+        cur, _ = o.prgd_step(cur, P.idx, P.y, P.n, P.r, eps_rel=1.0, alpha_scale=alpha_scale,
+                             step="adaptive" if steep else "constant")
+        if not steep and prev > 0 and rel > 2 * prev:
+            steep, fb = True, it + 1
+        prev = rel
+    return cur, fb
+
+
+def test_diverging_constant_step_falls_back_to_the_steepest_step():
+    # alpha_scale 5 on this planted problem: the relative residual goes
+    # 0.58, 0.84, 2.2 (more than doubling at iteration 3), so iterations from
+    # 4 on take the steepest step, which recovers the tensor
+    P = w.planted_small(6)
+    ref, fb = _oracle_with_fallback(P, 5.0, 12)
+    assert fb == 4
+    with ctx_for(P, precision=ttc.PREC_FP64, alpha_scale=5.0, stop_rule=ttc.STOP_NONE, max_iter=12) as c:
+        res = c.solve()
+        assert res["fallback_iter"] == fb
+        assert o.tt_dist(c.get_cores(), ref) <= 1e-9 * o.tt_norm(ref)
+    with ctx_for(P, precision=ttc.PREC_FP64, alpha_scale=5.0, stop_rule=ttc.STOP_RELERR, tol=1e-9,
+                 max_iter=200) as c:
+        c.set_truth(P.truth)
+        res = c.solve()
+        assert res["converged"] and res["fallback_iter"] == fb
+        assert c.relerr() <= 1e-9
+        # a second solve starts again from the configured constant step
+        c.set_cores(P.init)
+        again = c.solve()
+        assert again["fallback_iter"] == fb and again["iters"] == res["iters"]
+    # with the fallback off the same iteration keeps diverging
+    with ctx_for(P, precision=ttc.PREC_FP64, alpha_scale=5.0, step_fallback=0, stop_rule=ttc.STOP_NONE,
+                 max_iter=6) as c:
+        res = c.solve()
+        assert res["fallback_iter"] == -1
+        assert o.tt_dist(c.get_cores(), P.truth) > o.tt_norm(P.truth)
+
+
+def test_fallback_in_the_server_matches_solve_alone():
+    P = w.planted_small(6)
+    opts = dict(precision=ttc.PREC_FP64, alpha_scale=5.0, stop_rule=ttc.STOP_RELERR, tol=1e-9, max_iter=200)
+    with ctx_for(P, **opts) as c:
+        c.set_truth(P.truth)
+        alone = c.solve()
+        cores = c.get_cores()
+    Q = w.planted_small(7)
+    with ttc.Server(max_slots=4) as srv:
+        t0 = srv.submit(Q.n, Q.r, Q.idx, Q.y, Q.init, truth=Q.truth,
+                        options=ttc.default_options(precision=ttc.PREC_FP64, stop_rule=ttc.STOP_RELERR, tol=1e-9))
+        t1 = srv.submit(P.n, P.r, P.idx, P.y, P.init, truth=P.truth, options=ttc.default_options(**opts))
+        other, res = srv.poll(t0), srv.poll(t1)
+    assert other["converged"]
+    assert res["converged"] and res["iters"] == alone["iters"]
+    for a, b in zip(res["cores"], cores):
+        assert np.array_equal(a, b)

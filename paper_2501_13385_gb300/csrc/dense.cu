@@ -78,6 +78,7 @@ struct Stage {
   int which;         // metric stages: 0 truth, 1 previous iterate
   int nmap;          // slice maps run by the first blocks
   int map_k[2];
+  int map_nb[2];     // blocks of each map on the block-per-slice path (slices strided over them)
   Job job[TTC_MAXM + 4];
 };
 
@@ -578,15 +579,18 @@ __device__ void ff_mm_rows(int M, int N, int K, const float2* A, int lda, const 
 // triangle (row by row, j >= i) of a rows x rows result when `sym`, else
 // row-major rows x cols
 __device__ __forceinline__ int ff_output(int u, bool sym, int rows, int cols) {
-  int p = threadIdx.x + u * blockDim.x;
+  const int p = threadIdx.x + u * blockDim.x;
   if (sym) {
     if (p >= rows * (rows + 1) / 2) return -1;
-    int r = 0;
-    while (p >= rows - r) {
-      p -= rows - r;
-      ++r;
-    }
-    return (r << 16) | (r + p);
+    // row r starts at r n - r (r - 1) / 2: invert the quadratic in FP32
+    // (exact integers below 2^24), then correct a rounding off by one
+    const float b = 2.f * rows + 1.f;
+    int r = (int)floorf(0.5f * (b - sqrtf(b * b - 8.f * (float)p)));
+    r = max(0, min(r, rows - 1));
+    if (r * rows - r * (r - 1) / 2 > p) --r;
+    else if ((r + 1) * rows - (r + 1) * r / 2 <= p) ++r;
+    const int start = r * rows - r * (r - 1) / 2;
+    return (r << 16) | (r + p - start);
   }
   if (p >= rows * cols) return -1;
   return ((p / cols) << 16) | (p - (p / cols) * cols);
@@ -707,8 +711,8 @@ __device__ void stage_job_ff(const DevProb& P, const Job& J, int b, double* smd)
   }
 }
 
-// new core k at slice x in an FP32 step (the sums of slice_map in float-float)
-__device__ void slice_map_ff(const DevProb& P, int k, int x, double* smd) {
+// new core k at slices b, b + nb, ... (the sums of slice_map in float-float)
+__device__ void slice_map_ff(const DevProb& P, int k, int b, int nb, double* smd) {
   float2* sm = reinterpret_cast<float2*>(smd);
   const int m = P.m;
   const int qa = P.q[k], qb = P.q[k + 1];
@@ -720,39 +724,42 @@ __device__ void slice_map_ff(const DevProb& P, int k, int x, double* smd) {
   float2* Ct = Sf + reg;           // C^T: qb x qa
   float2* Cp = Ct + reg;           // C' = S_{k-1} C: ra x qb
   float2* Pt = Cp + reg;           // P_k^T: rb x qb
-  const double* C = P.C[k] + (long long)x * qa * qb;
-  const int ldC = ff_ld(qb);
-  if (k > 0) {
-    const int ldS = ff_ld(qa);
-    ff_stage(Sf, ldS, P.small + P.off_sk[k - 1], ra, qa, qa, false);
-    ff_stage(Ct, ldS, C, qa, qb, qb, true);
-    __syncthreads();
-    ff_mm_rows(ra, qb, qa, Sf, ldS, Ct, ldS, Cp, ldC);
-  } else {
-    ff_stage(Cp, ldC, C, qa, qb, qb, false);   // C' = C (qa = ra = 1)
-  }
+  const int ldC = ff_ld(qb), ldS = ff_ld(qa);
+  // the fixed factors once per block: S_{k-1} and P_k^T
+  if (k > 0) ff_stage(Sf, ldS, P.small + P.off_sk[k - 1], ra, qa, qa, false);
   if (k < m - 1) ff_stage(Pt, ldC, P.small + P.off_pk[k], qb, rb, rb, true);
-  __syncthreads();
-  // Remark 3.6: the rounding ran on W^{1/2} W_l; undo the weight
-  const double wu = P.weighted_retraction ? sqrt(gpow(P, k, x, -1)) : 1.0;
-  double* T = P.core64[k] + (long long)x * ra * rb;
-  float* T32 = P.core32p[k] + (long long)x * P.R * P.R;
-  double* T64 = P.core64p[k] + (long long)x * P.R * P.R;
-  for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
-    const int a = i / rb, bcol = i - (i / rb) * rb;
-    double v;
-    if (k < m - 1) {
-      float s, c;
-      ffa::dot(Cp + a * ldC, Pt + bcol * ldC, qb, s, c);
-      v = ffa::join(s, c);
+  for (int x = b; x < P.n[k]; x += nb) {
+    __syncthreads();   // the fixed factors are staged, the previous slice's reads are done
+    const double* C = P.C[k] + (long long)x * qa * qb;
+    if (k > 0) {
+      ff_stage(Ct, ldS, C, qa, qb, qb, true);
+      __syncthreads();
+      ff_mm_rows(ra, qb, qa, Sf, ldS, Ct, ldS, Cp, ldC);
     } else {
-      const float2 e = Cp[a * ldC + bcol];
-      v = ffa::join(e.x, e.y);
+      ff_stage(Cp, ldC, C, qa, qb, qb, false);   // C' = C (qa = ra = 1)
     }
-    if (P.weighted_retraction) v *= wu;
-    T[i] = v;
-    T32[pad_idx(P, k, a, bcol)] = (float)v;
-    T64[pad_idx(P, k, a, bcol)] = v;
+    __syncthreads();
+    // Remark 3.6: the rounding ran on W^{1/2} W_l; undo the weight
+    const double wu = P.weighted_retraction ? sqrt(gpow(P, k, x, -1)) : 1.0;
+    double* T = P.core64[k] + (long long)x * ra * rb;
+    float* T32 = P.core32p[k] + (long long)x * P.R * P.R;
+    double* T64 = P.core64p[k] + (long long)x * P.R * P.R;
+    for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
+      const int a = i / rb, bcol = i - (i / rb) * rb;
+      double v;
+      if (k < m - 1) {
+        float s, c;
+        ffa::dot(Cp + a * ldC, Pt + bcol * ldC, qb, s, c);
+        v = ffa::join(s, c);
+      } else {
+        const float2 e = Cp[a * ldC + bcol];
+        v = ffa::join(e.x, e.y);
+      }
+      if (P.weighted_retraction) v *= wu;
+      T[i] = v;
+      T32[pad_idx(P, k, a, bcol)] = (float)v;
+      T64[pad_idx(P, k, a, bcol)] = v;
+    }
   }
 }
 
@@ -763,6 +770,38 @@ __device__ void slice_map_ff(const DevProb& P, int k, int x, double* smd) {
 // memory.  With `check`, a non-finite total flags the step.
 __device__ void sum_rows(const DevProb& P, const double* src, int n, int d, double* dst, double* sm, bool check) {
   const int groups = max(1, min((int)blockDim.x / max(d, 1), 32));
+  if (groups == 1) {
+    // wide rows: each thread sums whole columns, two at a time with eight
+    // rows of each in flight (the partials come from L2, whose latency
+    // sets the time of this serial tail of a stage), in a fixed order
+    const int bd = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < d; i0 += 2 * bd) {
+      const int i1 = i0 + bd;
+      const bool two = i1 < d;
+      double a[8], c[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = c[u] = 0.0;
+      for (int bb = 0; bb < n; bb += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (bb + u < n) {
+            a[u] += __ldcg(src + (long long)(bb + u) * d + i0);
+            if (two) c[u] += __ldcg(src + (long long)(bb + u) * d + i1);
+          }
+        }
+      }
+      const double t0 = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+      dst[i0] = t0;
+      if (check && !isfinite(t0)) atomicOr(P.flags, 1u);
+      if (two) {
+        const double t1 = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+        dst[i1] = t1;
+        if (check && !isfinite(t1)) atomicOr(P.flags, 1u);
+      }
+    }
+    __syncthreads();
+    return;
+  }
   for (int base = 0; base < d; base += blockDim.x / groups) {
     const int per = blockDim.x / groups;
     const int g = threadIdx.x / per, i = base + (threadIdx.x - g * per);
@@ -846,14 +885,18 @@ __global__ void __launch_bounds__(kThreads) k_stage(const DevProb P, const Stage
   int b = blockIdx.x;
   for (int i = 0; i < S.nmap; ++i) {     // slice maps first
     const int k = S.map_k[i];
-    if (b < P.n[k]) {
-      if (P.dense_ff)
-        slice_map_ff(P, k, b, sm);
-      else
-        slice_map(P, k, b, sm);
+    if (b < S.map_nb[i]) {
+      if (P.dense_ff) {
+        slice_map_ff(P, k, b, S.map_nb[i], sm);
+      } else {
+        for (int x = b; x < P.n[k]; x += S.map_nb[i]) {
+          __syncthreads();   // the previous slice's scratch reads are done
+          slice_map(P, k, x, sm);
+        }
+      }
       return;
     }
-    b -= P.n[k];
+    b -= S.map_nb[i];
   }
   int j = 0;
   while (b >= S.job[j].nb) {
@@ -1150,9 +1193,16 @@ __device__ __forceinline__ void build_C_w_body(const DevProb& P, int blk, int ns
   double* t1 = scr + wscr_mat(P);
   double* B = scr + 2 * wscr_mat(P);
   warp_load(Tt, P.core64[k] + (long long)x * ra * rb, ra * rb);
-  warp_mm(t1, P.small + P.off_lami[k], ra, P.E[k] + (long long)x * ra * rb, rb, ra, rb, ra);
-  warp_mm_scaled(B, t1, rb, P.small + P.off_gami[k + 1], rb, ra, rb, rb, -alpha * wi);
-  if (k + 1 < m) {
+  if (P.steepest) {
+    // the steepest step formed B1 = B / alpha already (k_build_B1)
+    const double* B1 = P.B1[k] + (long long)x * ra * rb;
+    for (int e = lane; e < ra * rb; e += 32) B[e] = alpha * B1[e];
+    __syncwarp();
+  } else {
+    warp_mm(t1, P.small + P.off_lami[k], ra, P.E[k] + (long long)x * ra * rb, rb, ra, rb, ra);
+    warp_mm_scaled(B, t1, rb, P.small + P.off_gami[k + 1], rb, ra, rb, rb, -alpha * wi);
+  }
+  if (k + 1 < m && !P.steepest) {
     const double* Q = P.small + P.off_qm[k];
     for (int e = lane; e < ra * rb; e += 32) {
       const int i = e / rb, j = e - (e / rb) * rb;
@@ -1260,6 +1310,72 @@ __global__ void __launch_bounds__(256) k_save_prev_batch(const DevProb* __restri
 // -sum_k [T..B1_k..T]) and G_k(x)^{1/(2m)} <Lam_k B1_k(x) Gam_{k+1}, B1_k(x)>:
 // summed over all slices this is ||Z||_W^2, because the components of Z are
 // W-orthogonal (Lemma 3.4) and Lam, Gam are the Grams of W^{1/2} T.
+// The same sums in float-float (FP32 steps, ff.cuh): operands staged as
+// float pairs in `sm` (seven regions of rmax (rmax + 1) pairs), every
+// product rows against rows.
+__device__ void build_B1_ff(const DevProb& P, int k, int x, int slice, float2* sm, double* red) {
+  const int m = P.m, ra = P.r[k], rb = P.r[k + 1];
+  int rm = 1;
+  for (int t = 0; t <= m; ++t) rm = max(rm, P.r[t]);
+  const int reg = rm * (rm + 1);
+  float2* Li = sm;                 // Lam_k^{-1}: ra x ra      -> Lam_k
+  float2* Et = Li + reg;           // E^T: rb x ra             -> Y^T = (Lam B1)^T: rb x ra
+  float2* Gt = Et + reg;           // (Gam_{k+1}^{-1})^T: rb x rb -> Gam_{k+1}
+  float2* Tm = Gt + reg;           // T: ra x rb
+  float2* Qt = Tm + reg;           // Q_k^T: rb x rb
+  float2* t1 = Qt + reg;           // Lam^{-1} E: ra x rb
+  float2* Bt = t1 + reg;           // B1^T: rb x ra
+  const int la = ff_ld(ra), lb = ff_ld(rb);
+  ff_stage(Li, la, P.small + P.off_lami[k], ra, ra, ra, false);
+  ff_stage(Et, la, P.E[k] + (long long)x * ra * rb, ra, rb, rb, true);
+  ff_stage(Gt, lb, P.small + P.off_gami[k + 1], rb, rb, rb, true);
+  if (k + 1 < m) {
+    ff_stage(Tm, lb, P.core64[k] + (long long)x * ra * rb, ra, rb, rb, false);
+    ff_stage(Qt, lb, P.small + P.off_qm[k], rb, rb, rb, true);
+  }
+  __syncthreads();
+  ff_mm_rows(ra, rb, ra, Li, la, Et, la, t1, lb);                 // t1 = Lam^{-1} E
+  __syncthreads();
+  const float2 wneg = ffa::split(-gpow(P, k, x, -1));
+  double* out = P.B1[k] + (long long)x * ra * rb;
+  float* out32 = P.B1_32p[k] + (long long)x * P.R * P.R;
+  double* out64 = P.B1_64p[k] + (long long)x * P.R * P.R;
+  for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
+    const int a = i / rb, b = i - (i / rb) * rb;
+    float s, c, as = 0.f, ac = 0.f;
+    ffa::dot(t1 + a * lb, Gt + b * lb, rb, s, c);
+    ffa::acc_scaled(as, ac, wneg, s, c);                          // -w t1 Gam^{-1}
+    if (k + 1 < m) {
+      ffa::dot(Tm + a * lb, Qt + b * lb, rb, s, c);
+      ffa::acc_scaled(as, ac, make_float2(1.f, 0.f), s, c);       // + T Q
+    }
+    const double v = ffa::join(as, ac);
+    out[i] = v;
+    const int pi = pad_idx(P, k, a, b);
+    out32[pi] = (float)v;
+    out64[pi] = v;
+    Bt[b * la + a] = ffa::renorm(as, ac);
+  }
+  __syncthreads();
+  // ||Z||_W^2 term: G^{1/(2m)} <Lam B1 Gam, B1>
+  ff_stage(Li, la, P.small + P.off_lam[k], ra, ra, ra, false);
+  ff_stage(Gt, lb, P.small + P.off_gam[k + 1], rb, rb, rb, false);
+  __syncthreads();
+  ff_mm_rows(rb, ra, ra, Bt, la, Li, la, Et, la);                  // (Lam B1)^T = B1^T Lam (Lam symmetric)
+  __syncthreads();
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) {
+    const int a = i / rb, b = i - (i / rb) * rb;
+    // (Lam B1 Gam)(a, b) = sum_c (Lam B1)(a, c) Gam(c, b): column a of (Lam B1)^T
+    float s = 0.f, c = 0.f;
+    for (int t = 0; t < rb; ++t) ffa::dot_step(s, c, Et[t * la + a], Gt[b * lb + t]);
+    const float2 bv = Bt[b * la + a];
+    acc += ffa::join(s, c) * ffa::join(bv.x, bv.y);
+  }
+  const double tot = blk_sum(acc, red);
+  if (threadIdx.x == 0) P.zw[slice] = gpow(P, k, x, +1) * tot;
+}
+
 __global__ void __launch_bounds__(128) k_build_B1(const DevProb P) {
   __shared__ double t1[TTC_MAXR * TTC_MAXR];
   __shared__ double B[TTC_MAXR * TTC_MAXR];
@@ -1271,6 +1387,11 @@ __global__ void __launch_bounds__(128) k_build_B1(const DevProb P) {
     ++k;
   }
   const int x = blk, m = P.m;
+  if (P.dense_ff) {
+    extern __shared__ __align__(16) float2 ffsm[];
+    build_B1_ff(P, k, x, slice, ffsm, red);
+    return;
+  }
   const int ra = P.r[k], rb = P.r[k + 1];
   const double wi = gpow(P, k, x, -1);
   const double* T = P.core64[k] + (long long)x * ra * rb;
@@ -1512,13 +1633,20 @@ __global__ void __launch_bounds__(128) k_build_C(const DevProb P) {
   const double wi = gpow(P, k, x, -1);
   const double* T = P.core64[k] + (long long)x * ra * rb;
   const double* E = P.E[k] + (long long)x * ra * rb;
-  blk_gemm<double>(ra, rb, ra, P.small + P.off_lami[k], ra, false, E, rb, false, t1, rb, 1.0, false);
-  __syncthreads();
-  blk_gemm<double>(ra, rb, rb, t1, rb, false, P.small + P.off_gami[k + 1], rb, false, B, rb, -alpha * wi, false);
-  __syncthreads();
-  if (k + 1 < m) {
-    blk_gemm<double>(ra, rb, rb, T, rb, false, P.small + P.off_qm[k], rb, false, B, rb, alpha, true);
+  if (P.steepest) {
+    // the steepest step formed B1 = B / alpha already (k_build_B1)
+    const double* B1 = P.B1[k] + (long long)x * ra * rb;
+    for (int i = threadIdx.x; i < ra * rb; i += blockDim.x) B[i] = alpha * B1[i];
     __syncthreads();
+  } else {
+    blk_gemm<double>(ra, rb, ra, P.small + P.off_lami[k], ra, false, E, rb, false, t1, rb, 1.0, false);
+    __syncthreads();
+    blk_gemm<double>(ra, rb, rb, t1, rb, false, P.small + P.off_gami[k + 1], rb, false, B, rb, -alpha * wi, false);
+    __syncthreads();
+    if (k + 1 < m) {
+      blk_gemm<double>(ra, rb, rb, T, rb, false, P.small + P.off_qm[k], rb, false, B, rb, alpha, true);
+      __syncthreads();
+    }
   }
   const int qa = P.q[k], qb = P.q[k + 1];
   double* C = P.C[k] + (long long)x * qa * qb;
@@ -1600,6 +1728,7 @@ struct Plan {
   std::vector<Stage> sweep;      // bond k (+ map of core k-1), then the final maps
   std::vector<Stage> metric[2];  // Gram sweep of ||A - B||^2, which = 0 truth, 1 previous
   size_t smem_stage = 0;
+  size_t smem_b1 = 0;         // float-float k_build_B1: seven regions of rmax (rmax + 1) float pairs
   bool warp = false;          // warp-per-slice kernels (ranks <= 8)
   size_t smem_warp = 0;
   double* metric_part = nullptr;
@@ -1614,11 +1743,35 @@ Plan& plan_of(const ttc_ctx* c) {
 }
 
 inline int nblocks_for(int nk) { return std::max(1, std::min(nk, 1024)); }
+
+// Blocks of a block-per-slice job: slices are strided over the blocks, each
+// block taking enough slices for about kBlockWork FMAs (at most
+// kMaxSlicesPerBlock: a slice costs a block a few dependent global-memory
+// round trips however small it is), so that a block's fixed costs (its
+// partial, the reduction protocol) are amortised and the reduction has fewer
+// partials.  `work` is one slice's FMAs.
+constexpr double kBlockWork = 131072.0;
+constexpr int kMaxSlicesPerBlock = 8;
+inline int nblocks_work(long long nk, double work) {
+  const double per = std::min((double)kMaxSlicesPerBlock, std::max(1.0, std::floor(kBlockWork / std::max(work, 1.0))));
+  return (int)std::max(1LL, std::min<long long>(1024, (long long)std::ceil((double)nk / per)));
+}
+// one slice's FMAs of each job (upper triangles of the symmetric Grams), and of a slice map
+inline double slice_work(int op, int ra, int rb, int qa, int qb, int k) {
+  switch (op) {
+    case OP_LAM: return (double)ra * ra * rb + 0.5 * rb * (rb + 1) * ra;
+    case OP_GAM: return (double)ra * rb * rb + 0.5 * ra * (ra + 1) * rb;
+    case OP_H: return (double)rb * rb * ra;
+    case OP_PSI: return (double)qa * qb * qb + 0.5 * qa * (qa + 1) * qb;
+    default: return k == 0 ? 0.5 * qb * (qb + 1) * qa : (double)qb * ra * qa + 0.5 * qb * (qb + 1) * ra;   // OP_N
+  }
+}
+inline double map_work(int ra, int rb, int qa, int qb) { return (double)ra * qb * qa + (double)ra * rb * qb; }
 inline int nblocks_warp(int nk) { return std::max(1, std::min((nk + kWarpsW - 1) / kWarpsW, 256)); }
 
 int launch_stage(ttc_ctx* c, const Stage& S, size_t smem) {
   int nb = 0;
-  for (int i = 0; i < S.nmap; ++i) nb += (int)c->n[S.map_k[i]];
+  for (int i = 0; i < S.nmap; ++i) nb += S.map_nb[i];
   for (int j = 0; j < S.njob; ++j) nb += S.job[j].nb;
   k_stage<<<nb, kThreads, smem, c->stream>>>(c->hp, S);
   TTC_CUDA(cudaGetLastError());
@@ -1747,7 +1900,9 @@ int ttc_alloc_dense(ttc_ctx* c) {
     Job J;
     J.op = op;
     J.k = k;
-    J.nb = warp_jobs ? nblocks_warp((int)c->n[k]) : nblocks_for((int)c->n[k]);
+    J.nb = warp_jobs  ? nblocks_warp((int)c->n[k])
+           : op <= OP_N ? nblocks_work(c->n[k], slice_work(op, c->r[k], c->r[k + 1], P.q[k], P.q[k + 1], k))
+                        : nblocks_for((int)c->n[k]);
     J.rows = rows;
     J.cols = cols;
     J.red = red;
@@ -1778,11 +1933,13 @@ int ttc_alloc_dense(ttc_ctx* c) {
     S.job[S.njob++] = mk(OP_PSI, k, P.q[k], P.q[k], P.off_psi[k]);
     pl.psi.push_back(S);
   }
+  auto map_nb = [&](int k) { return nblocks_work(c->n[k], map_work(c->r[k], c->r[k + 1], P.q[k], P.q[k + 1])); };
   for (int k = 0; k + 1 < m; ++k) {
     Stage S = blank();
     if (k > 0) {
       S.nmap = 1;
       S.map_k[0] = k - 1;
+      S.map_nb[0] = map_nb(k - 1);
     }
     S.job[S.njob++] = mk(OP_N, k, P.q[k + 1], P.q[k + 1], P.off_nk[k]);
     S.post = POST_BOND;
@@ -1792,7 +1949,9 @@ int ttc_alloc_dense(ttc_ctx* c) {
   {
     Stage S = blank();
     S.nmap = 0;
+    S.map_nb[S.nmap] = map_nb(m - 2);
     S.map_k[S.nmap++] = m - 2;
+    S.map_nb[S.nmap] = map_nb(m - 1);
     S.map_k[S.nmap++] = m - 1;
     pl.sweep.push_back(S);
   }
@@ -1844,6 +2003,7 @@ int ttc_alloc_dense(ttc_ctx* c) {
   pl.smem_stage = std::max(std::max(red_need, ff_need), std::max(proj_need, bond_need)) + 64;
   pl.smem_warp = pl.warp ? std::max(pl.smem_stage, sizeof(double) * (size_t)kWarpsW * 3 * wscr_mat_host(P))
                          : pl.smem_stage;
+  pl.smem_b1 = sizeof(float2) * (size_t)(7 * rmax * (rmax + 1));
   {
     // the attribute is per device and shared by every context: only raise it,
     // so that contexts needing more than this one keep launching
@@ -1852,6 +2012,12 @@ int ttc_alloc_dense(ttc_ctx* c) {
     std::lock_guard<std::mutex> lk(mu);
     int dev = 0;
     TTC_CUDA(cudaGetDevice(&dev));
+    static std::map<int, bool> b1_granted;
+    if (!b1_granted[dev]) {   // the largest float-float k_build_B1 (rank 32)
+      TTC_CUDA(cudaFuncSetAttribute(k_build_B1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(float2) * 7 * TTC_MAXR * (TTC_MAXR + 1))));
+      b1_granted[dev] = true;
+    }
     if (granted[dev] < pl.smem_warp) {
       const int sz = (int)pl.smem_warp;   // >= smem_stage
       TTC_CUDA(cudaFuncSetAttribute(k_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
@@ -1916,7 +2082,7 @@ int ttc_launch_dense(ttc_ctx* c) {
   int nslices = 0;
   for (int k = 0; k < m; ++k) nslices += (int)c->n[k];
   if (P.steepest) {   // alpha_l by exact line search before the rank-2r cores are formed
-    k_build_B1<<<nslices, 128, 0, st>>>(P);
+    k_build_B1<<<nslices, 128, P.dense_ff ? pl.smem_b1 : 0, st>>>(P);
     TTC_CUDA(cudaGetLastError());
     const int tb = tangent_blocks(P);
     if (P.step_fp64) {   // an FP64 step: ||P_Omega Z||^2 in FP64

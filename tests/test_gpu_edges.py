@@ -72,8 +72,10 @@ def test_empty_and_oversized_inputs_are_rejected():
     dict(n=[12, 10, 11, 13], r=[1, 12, 17, 11, 1], count=9000),
     dict(n=[64, 64, 64], r=[1, 32, 32, 1], count=100000),
 ], ids=lambda s: "r" + "-".join(map(str, s["r"][1:-1])))
-def test_float_float_dense_stages_match_oracle(spec):
-    # FP64 steps whose slice products (the Grams and the new cores) run in
+@pytest.mark.parametrize("steepest", [False, True], ids=["constant", "steepest"])
+def test_float_float_dense_stages_match_oracle(spec, steepest):
+    # FP64 steps whose slice products (the Grams, the new cores and, with the
+    # steepest step, the unit-step update cores B1 and ||Z||_W^2) run in
     # float-float, as every FP32 step's do: the products are accurate to
     # ~1e-11 relative to sum |a_i b_i| (compensated dot products of 48-bit
     # operands), so the step stays within 1e-8 of the oracle's (an FP32
@@ -81,12 +83,15 @@ def test_float_float_dense_stages_match_oracle(spec):
     # that the second starts from iterates the float-float path made
     P = w.random_problem(78, spec["n"], spec["r"], spec["count"], init_rel=0.1)
     cur = P.init
-    with ttc.Context(P.n, P.r, precision=ttc.PREC_FP64, dense_mode=ttc.DENSE_FF) as c:
+    rule = ttc.STEP_STEEPEST if steepest else ttc.STEP_CONSTANT
+    with ttc.Context(P.n, P.r, precision=ttc.PREC_FP64, dense_mode=ttc.DENSE_FF, step_rule=rule) as c:
         c.set_observations(P.idx, P.y)
         c.set_cores(P.init)
         for _ in range(2):
-            c.step()
-            cur, _ = o.prgd_step(cur, P.idx, P.y, P.n, P.r, eps_rel=1.0, alpha_scale=1.5)
+            info = c.step()
+            cur, oi = o.prgd_step(cur, P.idx, P.y, P.n, P.r, eps_rel=1.0, alpha_scale=1.5,
+                                  step="adaptive" if steepest else "constant")
+            assert info["alpha"] == pytest.approx(oi.alpha, rel=1e-8)
             assert o.tt_dist(c.get_cores(), cur) <= 1e-8 * o.tt_norm(cur)
 
 

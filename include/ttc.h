@@ -208,7 +208,9 @@ int ttc_get_slice_energy(ttc_ctx* ctx, int k, double* s_out);
 int ttc_get_scatter(ttc_ctx* ctx, int k, double* E_out);
 
 /* Layout of mode k, for checking: perm[N] (input position of the j-th entry
- * in mode-k order) and seg_off[n_k + 1] (CSR offsets of the slices). */
+ * in mode-k order: the stable sort by x_k of mode k-1's order, mode 0's of
+ * the input order, i.e. lexicographic in (x_k, x_{k-1}, ..., x_0, input
+ * position)) and seg_off[n_k + 1] (CSR offsets of the slices). */
 int ttc_get_layout(ttc_ctx* ctx, int k, int32_t* perm_out, int64_t* seg_off_out);
 
 /* Kernel timing: when enabled, the dominant kernel of every iteration (the
@@ -249,10 +251,15 @@ int ttc_batch_step(ttc_batch* b);
 /* Wait for all work enqueued by the batch. */
 int ttc_batch_sync(ttc_batch* b);
 /* Profiling: the batched sampled-pass launch(es) of every step are bracketed
- * by events (graph event-record nodes); each step then waits for the end
- * event and adds the duration. */
+ * by events (graph event-record nodes), and so is the dense part of the step
+ * (Lemma 3.5's projection, the step size and Algorithm 1's rounding of every
+ * member, from the end of the pass to the join of all members); each step
+ * then waits for the last event and adds both durations.
+ * ttc_batch_profile_read gives the pass's total, ttc_batch_profile_read_dense
+ * the dense part's (ms may be NULL), over `count` steps. */
 int ttc_batch_profile_enable(ttc_batch* b, int on);
 int ttc_batch_profile_read(ttc_batch* b, double* ms, int64_t* count, int reset);
+int ttc_batch_profile_read_dense(ttc_batch* b, double* ms, int64_t* count, int reset);
 /* Kernels launched by the batch so far (all graph kernel nodes of each step). */
 int ttc_batch_launch_count(ttc_batch* b, int64_t* launches);
 void ttc_batch_destroy(ttc_batch* b);

@@ -38,8 +38,9 @@ struct ttc_batch {
   long long kernels_per_step = 0;
   long long nlaunch = 0;
   bool prof = false;
-  cudaEvent_t ev_beg = nullptr, ev_end = nullptr;
-  double prof_ms = 0.0;
+  cudaEvent_t ev_beg = nullptr, ev_end = nullptr;     // the pass
+  cudaEvent_t ev_dbeg = nullptr, ev_dend = nullptr;   // the dense part
+  double prof_ms = 0.0, prof_dense_ms = 0.0;
   long long prof_count = 0;
 };
 
@@ -201,6 +202,7 @@ int capture(ttc_batch* b) {
       ++batched;
     }
   if (s == TTC_OK && e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
+  if (b->prof && s == TTC_OK && e == cudaSuccess) e = cudaEventRecordWithFlags(b->ev_dbeg, b->stream, cudaEventRecordExternal);
   long long dense_kernels = 0;
   for (size_t i = 1; i < b->dense.size() && s == TTC_OK && e == cudaSuccess; ++i) {
     cudaStream_t ds = b->dstreams[i - 1];
@@ -228,6 +230,7 @@ int capture(ttc_batch* b) {
     }
     c->stream = saved;
   }
+  if (b->prof && s == TTC_OK && e == cudaSuccess) e = cudaEventRecordWithFlags(b->ev_dend, b->stream, cudaEventRecordExternal);
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
   long long kernels = batched + dense_kernels;
   for (size_t i = 0; i < b->members.size(); ++i) {
@@ -278,6 +281,8 @@ int ttc_batch_create(ttc_batch** out, ttc_ctx* const* members, int count, void* 
   for (int i = 0; i < count && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev_beg);
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev_end);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev_dbeg);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->ev_dend);
   if (e != cudaSuccess) {
     ttc_record_cuda_error(e);
     ttc_batch_destroy(b);
@@ -314,10 +319,12 @@ int ttc_batch_step(ttc_batch* b) {
     }
   }
   if (b->prof) {
-    TTC_CUDA(cudaEventSynchronize(b->ev_end));
-    float t = 0.f;
+    TTC_CUDA(cudaEventSynchronize(b->ev_dend));
+    float t = 0.f, td = 0.f;
     TTC_CUDA(cudaEventElapsedTime(&t, b->ev_beg, b->ev_end));
+    TTC_CUDA(cudaEventElapsedTime(&td, b->ev_dbeg, b->ev_dend));
     b->prof_ms += t;
+    b->prof_dense_ms += td;
     b->prof_count += 1;
   }
   return TTC_OK;
@@ -348,6 +355,19 @@ int ttc_batch_profile_read(ttc_batch* b, double* ms, int64_t* count, int reset) 
   if (count) *count = b->prof_count;
   if (reset) {
     b->prof_ms = 0.0;
+    b->prof_dense_ms = 0.0;
+    b->prof_count = 0;
+  }
+  return TTC_OK;
+}
+
+int ttc_batch_profile_read_dense(ttc_batch* b, double* ms, int64_t* count, int reset) {
+  if (!b) return TTC_EINVAL;
+  if (ms) *ms = b->prof_dense_ms;
+  if (count) *count = b->prof_count;
+  if (reset) {
+    b->prof_ms = 0.0;
+    b->prof_dense_ms = 0.0;
     b->prof_count = 0;
   }
   return TTC_OK;
@@ -372,6 +392,8 @@ void ttc_batch_destroy(ttc_batch* b) {
     if (ev) cudaEventDestroy(ev);
   if (b->ev_beg) cudaEventDestroy(b->ev_beg);
   if (b->ev_end) cudaEventDestroy(b->ev_end);
+  if (b->ev_dbeg) cudaEventDestroy(b->ev_dbeg);
+  if (b->ev_dend) cudaEventDestroy(b->ev_dend);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }

@@ -1577,9 +1577,12 @@ __global__ void __launch_bounds__(kTanThreads) k_tangent_sq(const DevProb P, int
   // the longest prefix table: rows of l_T and l_Z over modes < j0
   const int tp = P.m >= 2 ? P.pre_tab[P.m - 1] : -1;
   const int j0 = tp >= 0 ? P.tab_j[tp] : 0;
+  // entries in the layout order of mode j0 - 1, lexicographic in
+  // (x_{j0-1}, ..., x_0): the lanes of a warp mostly share their table rows
+  const int ord = tp >= 0 ? j0 - 1 : P.m - 1;
   double acc = 0.0;
   for (int e = blockIdx.x * kTanThreads + threadIdx.x; e < P.N; e += gridDim.x * kTanThreads) {
-    const Code w = load_code(P, 0, e);
+    const Code w = load_code(P, ord, e);
     T lT[RC], lZ[RC];
 #pragma unroll
     for (int a = 0; a < RC; ++a) {

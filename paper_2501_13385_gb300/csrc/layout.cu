@@ -1,7 +1,11 @@
 // Omega layout builder (once per problem): validates the observed index set,
 // packs coordinates into 32-bit code words, and for every mode k builds the
-// stable order of the entries by x_k (ties keep input order) with the CSR
-// offsets of the mode-k slices and the chunk lists the sampled pass walks.
+// stable order of the entries by x_k with the CSR offsets of the mode-k
+// slices and the chunk lists the sampled pass walks.  Mode k's order is the
+// stable sort by x_k of mode k-1's (mode 0's of the input order), so it is
+// lexicographic in (x_k, x_{k-1}, ..., x_0): inside a mode-k slice, entries
+// that share the prefix (x_0 .. x_{k-1}) are adjacent, and the prefix-table
+// rows the passes read for them are read by neighbouring lanes.
 // Duplicate indices are found by a lexicographic order built from the same
 // stable per-mode sort (LSD over modes d..1).  Problem statement: Omega is a
 // set of observed indices and P_Omega samples T on it (Eq. (model: Low TT)).
@@ -240,7 +244,7 @@ __global__ void k_chunk_fill(const int* __restrict__ cfirst, int nk, int* __rest
 inline int nblk(long long n, int bs) { return (int)((n + bs - 1) / bs); }
 
 // stable LSD radix sort of perm_in by the coordinate of mode k (8-bit digits)
-int sort_by_mode(ttc_ctx* c, const uint32_t* code, int* perm_in, int* perm_out, int* tmp_perm, int k,
+int sort_by_mode(ttc_ctx* c, const uint32_t* code, const int* perm_in, int* perm_out, int* tmp_perm, int k,
                  int* counts, long long* bsum) {
   const DevProb& P = c->hp;
   int N = P.N;
@@ -374,8 +378,12 @@ int ttc_build_layout(ttc_ctx* c, const int32_t* idx_host, const double* y_host) 
       cleanup();
       return s;
     }
-    k_iota<<<nblk(N, 256), 256, 0, st>>>(pa, N);
-    if ((s = sort_by_mode(c, code_in, pa, perm, pt, k, counts, bsum)) != TTC_OK) { cleanup(); return s; }
+    const int* from = pa;
+    if (k == 0)
+      k_iota<<<nblk(N, 256), 256, 0, st>>>(pa, N);
+    else
+      from = P.perm[k - 1];   // chained: lexicographic in (x_k, ..., x_0)
+    if ((s = sort_by_mode(c, code_in, from, perm, pt, k, counts, bsum)) != TTC_OK) { cleanup(); return s; }
     k_gather_mode<<<nblk(N, 256), 256, 0, st>>>(perm, code_in, y_d, W, N, code_k, y32, y64);
     k_seg_bounds<<<nblk(N, 256), 256, 0, st>>>(perm, code_in, W, N, P.cword[k], P.cshift[k], P.cbits[k], nk, seg);
     k_chunk_counts<<<nblk(nk + 1, 256), 256, 0, st>>>(seg, nk, TTC_CHUNK, cfirst);

@@ -89,7 +89,7 @@ EXPORTS = [
     "ttc_get_slice_energy", "ttc_get_scatter", "ttc_get_layout", "ttc_profile_enable", "ttc_profile_read",
     "ttc_device_bytes", "ttc_destroy", "ttc_strerror", "ttc_last_cuda_error", "ttc_launch_count",
     "ttc_tt_dist2_static", "ttc_batch_create", "ttc_batch_step", "ttc_batch_sync", "ttc_batch_profile_enable",
-    "ttc_batch_profile_read", "ttc_batch_launch_count", "ttc_batch_destroy",
+    "ttc_batch_profile_read", "ttc_batch_profile_read_dense", "ttc_batch_launch_count", "ttc_batch_destroy",
     "ttc_server_create", "ttc_submit", "ttc_poll", "ttc_server_stats", "ttc_server_destroy",
 ]
 
@@ -131,6 +131,7 @@ def lib():
         "ttc_batch_sync": (C.c_int, [vp]),
         "ttc_batch_profile_enable": (C.c_int, [vp, C.c_int]),
         "ttc_batch_profile_read": (C.c_int, [vp, dp, i64p, C.c_int]),
+        "ttc_batch_profile_read_dense": (C.c_int, [vp, dp, i64p, C.c_int]),
         "ttc_batch_launch_count": (C.c_int, [vp, i64p]),
         "ttc_batch_destroy": (None, [vp]),
         "ttc_server_create": (C.c_int, [C.POINTER(vp), C.c_size_t, C.c_int, vp]),
@@ -349,6 +350,14 @@ class Batch:
         cnt = C.c_int64()
         _check(lib().ttc_batch_profile_read(self._h, C.byref(ms), C.byref(cnt), 1 if reset else 0),
                "ttc_batch_profile_read")
+        return ms.value, cnt.value
+
+    def profile_read_dense(self, reset: bool = False):
+        """(ms, steps) of the dense part of the profiled steps (end of the pass to the join of all members)."""
+        ms = C.c_double()
+        cnt = C.c_int64()
+        _check(lib().ttc_batch_profile_read_dense(self._h, C.byref(ms), C.byref(cnt), 1 if reset else 0),
+               "ttc_batch_profile_read_dense")
         return ms.value, cnt.value
 
     def launch_count(self) -> int:

@@ -69,9 +69,15 @@ def test_layout_bit_exact(shape):
     n, r, cnt = shape
     P = w.random_problem(11, n, r, cnt)
     with ctx_for(P) as c:
+        prev = np.arange(cnt)
         for k in range(P.m):
             perm, seg = c.layout(k)
-            assert np.array_equal(perm, np.argsort(P.idx[:, k], kind="stable"))
+            # mode k's order: the stable sort by x_k of mode k-1's order, so
+            # lexicographic in (x_k, ..., x_0, input position)
+            ref_perm = prev[np.argsort(P.idx[prev, k], kind="stable")]
+            assert np.array_equal(perm, ref_perm)
+            assert np.array_equal(perm, np.lexsort([np.arange(cnt)] + [P.idx[:, j] for j in range(k + 1)]))
+            prev = ref_perm
             ref = np.concatenate([[0], np.cumsum(np.bincount(P.idx[:, k], minlength=n[k]))])
             assert np.array_equal(seg, ref)
 

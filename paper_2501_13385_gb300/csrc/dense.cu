@@ -1540,33 +1540,95 @@ __device__ __forceinline__ void tangent_times(const DevProb& P, int j, int x, T 
   }
 }
 
+// row g of the tangent companion of table t (a prefix table over modes
+// 0..jt-1), from scratch by its own chain
+template <typename T, int R, int RC>
+__device__ __forceinline__ void ztable_row_chain(const DevProb& P, int t, long long g) {
+  const unsigned row = (unsigned)(g - P.tab_row0[t]);
+  const int jt = P.tab_j[t];
+  T lT[RC], lZ[RC];
+#pragma unroll
+  for (int a = 0; a < RC; ++a) {
+    lT[a] = 0;
+    lZ[a] = 0;
+  }
+  lT[0] = 1;
+  bool valid = true;
+  for (int j = 0; j < jt; ++j) {
+    const int x = (int)((row >> (P.cshift[j] - P.tab_shift[t])) & ((1u << P.cbits[j]) - 1u));
+    valid = valid && x < P.n[j];
+    if (valid) tangent_times<T, R, RC>(P, j, x, lT, lZ);
+  }
+  T* dst = ptab<T>(P, true) + g * R;
+#pragma unroll
+  for (int a = 0; a < R; ++a) dst[a] = (valid && a < RC && a < P.r[jt]) ? lZ[a < RC ? a : 0] : T(0);
+}
+
 // The tangent companion of the prefix tables: row i of ztab holds l_Z over
-// the table's modes (the prefix table itself holds l_T), one thread per row.
+// the table's modes (the prefix table itself holds l_T).  A block takes 128
+// consecutive rows; when they all belong to one two-mode prefix table and
+// share the coordinate of its second mode (its bits lie above the first
+// mode's), that mode's slices T_1(x_1), B1_1(x_1) are staged in shared memory
+// once and every row is l_Z = B1_0(x_0) T_1(x_1) + T_0(x_0) B1_1(x_1) from
+// the first mode's rows; otherwise each thread runs its row's chain.
 template <typename T, int R, int RC>
 __global__ void __launch_bounds__(128) k_build_ztables(const DevProb P) {
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < P.tab_total;
-       g += (long long)gridDim.x * blockDim.x) {
+  __shared__ __align__(16) T sS[R * R];
+  __shared__ __align__(16) T sB[R * R];
+  __shared__ long long key0;
+  for (long long g0 = (long long)blockIdx.x * blockDim.x; g0 < P.tab_total; g0 += (long long)gridDim.x * blockDim.x) {
+    const long long g = g0 + threadIdx.x;
+    const bool inr = g < P.tab_total;
     int t = 0;
-    while (t + 1 < P.ntab && g >= P.tab_row0[t + 1]) ++t;
-    if (P.tab_side[t] != 0) continue;   // suffix tables have no companion
-    const unsigned row = (unsigned)(g - P.tab_row0[t]);
-    const int jt = P.tab_j[t];
-    T lT[RC], lZ[RC];
-#pragma unroll
-    for (int a = 0; a < RC; ++a) {
-      lT[a] = 0;
-      lZ[a] = 0;
+    if (inr)
+      while (t + 1 < P.ntab && g >= P.tab_row0[t + 1]) ++t;
+    const bool pre = inr && P.tab_side[t] == 0;
+    const unsigned row = inr ? (unsigned)(g - P.tab_row0[t]) : 0u;
+    int x0 = 0, x1 = 0;
+    long long key = -1;
+    if (pre && P.tab_j[t] == 2) {
+      x0 = (int)((row >> (P.cshift[0] - P.tab_shift[t])) & ((1u << P.cbits[0]) - 1u));
+      x1 = (int)((row >> (P.cshift[1] - P.tab_shift[t])) & ((1u << P.cbits[1]) - 1u));
+      if (x1 < P.n[1]) key = (long long)t * (1LL << 32) + x1;
     }
-    lT[0] = 1;
-    bool valid = true;
-    for (int j = 0; j < jt; ++j) {
-      const int x = (int)((row >> (P.cshift[j] - P.tab_shift[t])) & ((1u << P.cbits[j]) - 1u));
-      valid = valid && x < P.n[j];
-      if (valid) tangent_times<T, R, RC>(P, j, x, lT, lZ);
-    }
-    T* dst = ptab<T>(P, true) + g * R;
+    __syncthreads();   // the previous rows' reads of sS, sB are done
+    if (threadIdx.x == 0) key0 = key;
+    __syncthreads();
+    if (__syncthreads_and(key >= 0 && key == key0)) {
+      const int r1 = P.r[1], r2 = P.r[2];
+      const T* S1 = pcore<T>(P, 1) + (long long)x1 * R * R;
+      const T* B11 = pb1<T>(P, 1) + (long long)x1 * R * R;
+      for (int i = threadIdx.x; i < R * R; i += blockDim.x) {
+        sS[i] = S1[i];
+        sB[i] = B11[i];
+      }
+      __syncthreads();
+      const bool valid = x0 < P.n[0];
+      T lT[RC], lZ[RC];
+      const T* S0 = pcore<T>(P, 0) + (long long)(valid ? x0 : 0) * R * R;
+      const T* B10 = pb1<T>(P, 0) + (long long)(valid ? x0 : 0) * R * R;
 #pragma unroll
-    for (int a = 0; a < R; ++a) dst[a] = (valid && a < RC && a < P.r[jt]) ? lZ[a < RC ? a : 0] : T(0);
+      for (int a = 0; a < RC; ++a) {
+        lT[a] = (valid && a < r1) ? S0[a] : T(0);    // row 0 of a 1 x r_1 slice
+        lZ[a] = (valid && a < r1) ? B10[a] : T(0);
+      }
+      T* dst = ptab<T>(P, true) + g * R;
+      for (int b = 0; b < R; ++b) {
+        T z = T(0);
+        if (valid && b < r2) {
+#pragma unroll
+          for (int a = 0; a < RC; ++a) {
+            if (a < r1) {
+              const int ix = r2 == 1 ? a : a * R + b;   // padded mirrors: a column when r_2 = 1
+              z = fma(lZ[a], sS[ix], fma(lT[a], sB[ix], z));
+            }
+          }
+        }
+        dst[b] = z;
+      }
+    } else if (pre) {
+      ztable_row_chain<T, R, RC>(P, t, g);
+    }
   }
 }
 

@@ -56,25 +56,98 @@ __device__ __forceinline__ void build_table_row(const DevProb& P, long long g) {
   store_row<R>(tab_ptr<T>(P) + g * R, v);
 }
 
+// Rows of a two-mode prefix table that share the second mode's coordinate
+// x_1 (its bits lie above the first mode's, so a block of consecutive rows
+// usually does) read the same slice T_1(x_1): a block whose rows all do
+// stages it in shared memory once, and each row is then T_0(x_0) T_1(x_1)
+// with the same FMA order as row_times (identical results).  `key` names
+// (problem, table, x_1) for that test, -1 when the row cannot take it.
+template <typename T, int R>
+__device__ __forceinline__ long long prefix2_key(const DevProb& P, long long g, int p, int& x0, int& x1) {
+  int t = 0;
+  while (t + 1 < P.ntab && g >= P.tab_row0[t + 1]) ++t;
+  if (P.tab_side[t] != 0 || P.tab_j[t] != 2) return -1;
+  const unsigned row = (unsigned)(g - P.tab_row0[t]);
+  x0 = (int)((row >> (P.cshift[0] - P.tab_shift[t])) & ((1u << P.cbits[0]) - 1u));
+  x1 = (int)((row >> (P.cshift[1] - P.tab_shift[t])) & ((1u << P.cbits[1]) - 1u));
+  if (x1 >= P.n[1]) return -1;
+  return ((long long)p * (2 * TTC_MAXM) + t) * (1LL << 32) + x1;
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void prefix2_row(const DevProb& P, long long g, int x0, const T* sS) {
+  const int r1 = P.r[1], r2 = P.r[2];
+  const bool valid = x0 < P.n[0];
+  const T* S0 = core_ptr<T>(P, 0) + (long long)(valid ? x0 : 0) * R * R;   // a 1 x r_1 slice: row 0
+  T l0[R], v[R];
+#pragma unroll
+  for (int a = 0; a < R; ++a) l0[a] = (valid && a < r1) ? S0[a] : T(0);
+#pragma unroll
+  for (int b = 0; b < R; ++b) {
+    T acc = 0;
+    if (valid && b < r2) {
+#pragma unroll
+      for (int a = 0; a < R; ++a)
+        if (a < r1) acc = fma(l0[a], sS[r2 == 1 ? a : a * R + b], acc);
+    }
+    v[b] = acc;
+  }
+  store_row<R>(tab_ptr<T>(P) + g * R, v);
+}
+
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_build_tables(const DevProb P) {
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < P.tab_total;
-       g += (long long)gridDim.x * blockDim.x)
-    build_table_row<T, R>(P, g);
+  __shared__ __align__(16) T sS[R * R];
+  __shared__ long long key0;
+  for (long long g0 = blockIdx.x * (long long)blockDim.x; g0 < P.tab_total; g0 += (long long)gridDim.x * blockDim.x) {
+    const long long g = g0 + threadIdx.x;
+    int x0 = 0, x1 = 0;
+    const long long key = g < P.tab_total ? prefix2_key<T, R>(P, g, 0, x0, x1) : -1;
+    __syncthreads();   // the previous rows' reads of sS are done
+    if (threadIdx.x == 0) key0 = key;
+    __syncthreads();
+    if (__syncthreads_and(key >= 0 && key == key0)) {
+      const T* S1 = core_ptr<T>(P, 1) + (long long)x1 * R * R;
+      for (int i = threadIdx.x; i < R * R; i += blockDim.x) sS[i] = S1[i];
+      __syncthreads();
+      prefix2_row<T, R>(P, g, x0, sS);
+    } else if (g < P.tab_total) {
+      build_table_row<T, R>(P, g);
+    }
+  }
 }
 
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_build_tables_batch(const DevProb* __restrict__ probs,
                                                             const long long* __restrict__ base, int nprob,
                                                             long long total) {
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
-       g += (long long)gridDim.x * blockDim.x) {
-    int lo = 0, hi = nprob - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (__ldg(base + mid) <= g) lo = mid; else hi = mid - 1;
+  __shared__ __align__(16) T sS[R * R];
+  __shared__ long long key0;
+  for (long long g0 = blockIdx.x * (long long)blockDim.x; g0 < total; g0 += (long long)gridDim.x * blockDim.x) {
+    const long long g = g0 + threadIdx.x;
+    int lo = 0;
+    if (g < total) {
+      int hi = nprob - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(base + mid) <= g) lo = mid; else hi = mid - 1;
+      }
     }
-    build_table_row<T, R>(probs[lo], g - __ldg(base + lo));
+    const DevProb& P = probs[lo];
+    const long long gl = g - __ldg(base + lo);
+    int x0 = 0, x1 = 0;
+    const long long key = g < total ? prefix2_key<T, R>(P, gl, lo, x0, x1) : -1;
+    __syncthreads();
+    if (threadIdx.x == 0) key0 = key;
+    __syncthreads();
+    if (__syncthreads_and(key >= 0 && key == key0)) {
+      const T* S1 = core_ptr<T>(P, 1) + (long long)x1 * R * R;
+      for (int i = threadIdx.x; i < R * R; i += blockDim.x) sS[i] = S1[i];
+      __syncthreads();
+      prefix2_row<T, R>(P, gl, x0, sS);
+    } else if (g < total) {
+      build_table_row<T, R>(P, gl);
+    }
   }
 }
 

@@ -71,7 +71,8 @@ def test_empty_and_oversized_inputs_are_rejected():
     dict(n=[40, 40, 40], r=[1, 20, 20, 1], count=48000),
     dict(n=[12, 10, 11, 13], r=[1, 12, 17, 11, 1], count=9000),
     dict(n=[64, 64, 64], r=[1, 32, 32, 1], count=100000),
-], ids=lambda s: "r" + "-".join(map(str, s["r"][1:-1])))
+    dict(n=[200, 30, 20], r=[1, 9, 10, 1], count=20000),   # 128-row groups of the two-mode prefix table
+], ids=lambda s: "r" + "-".join(map(str, s["r"][1:-1])) + "-n" + str(s["n"][0]))
 @pytest.mark.parametrize("steepest", [False, True], ids=["constant", "steepest"])
 def test_float_float_dense_stages_match_oracle(spec, steepest):
     # FP64 steps whose slice products (the Grams, the new cores and, with the

@@ -64,6 +64,8 @@ def parse():
                     help="requests of the mixed serving stream (0: skip)")
     ap.add_argument("--serve-max-entries", type=int, default=1_000_000)
     ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-probe", type=int, default=128,
+                    help="requests of the burst that probes the service rate (the Poisson stream runs at 70%% of it)")
     ap.add_argument("--headline-only", action="store_true",
                     help="time the headline batch only (no tolerance runs, other workloads, end to end, serving "
                          "or CPU baseline): the command the committed ncu launch lists profile")
@@ -658,9 +660,10 @@ def serving_stream(args, rank, ttc, w, np):
     2-16, |Omega| log-uniform in [1e3, max_entries], each request a seeded
     Gaussian-core truth with uniform Omega, solved to rel.err <= 1e-6 vs T*
     or 500 iterations with the steepest step (the safe step for unknown
-    problems: the constant step's tuned scale diverges on some of them); a
-    burst of all requests, then Poisson arrivals at 70% of the burst's
-    request rate.""" 
+    problems: the constant step's tuned scale diverges on some of them).
+    The service rate is probed by a burst of the first `serve_probe`
+    requests (all submitted at once); then all requests arrive as a Poisson
+    stream at 70% of that rate."""
     import multiprocessing as mp
     n = args.serve_mixed
     with mp.get_context("spawn").Pool(max(1, min(16, host_cores()))) as pool:
@@ -668,11 +671,12 @@ def serving_stream(args, rank, ttc, w, np):
     mopt = ttc.default_options(precision=ttc.PREC_MIXED, stop_rule=ttc.STOP_RELERR, tol=1e-6, max_iter=500,
                                step_rule=ttc.STEP_STEEPEST)
 
-    def run_stream(gaps):
+    def run_stream(gaps, sub=None):
+        sub = reqs if sub is None else sub
         with ttc.Server(max_slots=args.serve_slots) as srv:
             t0 = time.perf_counter()
             tk = []
-            for Q, gap in zip(reqs, gaps):
+            for Q, gap in zip(sub, gaps):
                 if gap > 0:
                     time.sleep(gap)
                 tk.append(srv.submit(Q.n, Q.r, Q.idx, Q.y, Q.init, truth=Q.truth, options=mopt))
@@ -691,8 +695,9 @@ def serving_stream(args, rank, ttc, w, np):
                 "engine_busy_ms": st["busy_ms"], "batch_rebuilds": st["rebuilds"],
                 "batch_rebuild_ms": st["rebuild_ms"], "admit_ms": st["admit_ms"]}
     phase(f"serving: {len(reqs)} requests generated")
-    burst = run_stream([0.0] * len(reqs))
-    phase("serving: burst done")
+    probe = reqs[:max(1, min(len(reqs), args.serve_probe))]
+    burst = run_stream([0.0] * len(probe), probe)
+    phase("serving: service-rate probe done")
     prng = np.random.default_rng(7)
     rate = 0.7 * burst["requests_per_s"]
     poisson = run_stream(list(prng.exponential(1.0 / rate, len(reqs))))
@@ -703,7 +708,7 @@ def serving_stream(args, rank, ttc, w, np):
             "omega_min": sizes[0], "omega_max": sizes[-1], "omega_median": sizes[len(sizes) // 2],
             "stop": "rel.err <= 1e-6 vs T* or 500 iterations, mixed precision, steepest step",
             "latency": "submission to completion; percentiles over converged requests",
-            "max_slots": args.serve_slots, "burst": burst, "poisson_70pct": poisson}
+            "max_slots": args.serve_slots, "burst_probe": burst, "poisson_70pct": poisson}
 
 
 def main():

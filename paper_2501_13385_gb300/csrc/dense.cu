@@ -880,7 +880,7 @@ __device__ bool stage_reduce(const DevProb& P, const Stage& S, int j, int b, dou
 }
 
 // ---- the stage kernel --------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_stage(const DevProb P, const Stage S) {
+__global__ void __launch_bounds__(kThreads, 3) k_stage(const DevProb P, const Stage S) {
   extern __shared__ __align__(16) double sm[];
   int b = blockIdx.x;
   for (int i = 0; i < S.nmap; ++i) {     // slice maps first
@@ -917,15 +917,24 @@ __global__ void __launch_bounds__(kThreads) k_stage(const DevProb P, const Stage
     for (int i = threadIdx.x; i < dd; i += blockDim.x) out[i] = acc[i];
   }
   if (!stage_reduce(P, S, j, b, sm)) return;   // the stage's last group finisher continues
-  if (S.post == POST_SMALL_PROJ) {
-    post_small_proj(P, sm);
-  } else if (S.post == POST_BOND) {
-    post_bond(P, S.post_k, sm);
-  } else if (S.post == POST_METRIC && S.post_k == P.m - 1 && threadIdx.x == 0) {
+  // (the small projection and the bond run in k_post, a one-block launch
+  // after this one: their shared memory would otherwise be reserved by every
+  // block of the stage and halve the blocks an SM holds)
+  if (S.post == POST_METRIC && S.post_k == P.m - 1 && threadIdx.x == 0) {
     double aa = P.small[P.off_mlam[0][P.m]], ab = P.small[P.off_mlam[1][P.m]], bbv = P.small[P.off_mlam[2][P.m]];
     P.scal[SC_METRIC] = aa - 2.0 * ab + bbv;
     P.scal[SC_NORM] = bbv;
   }
+}
+
+// the factorizations that follow a block-per-slice stage, on one block: the
+// Gram inverses and Q_k (POST_SMALL_PROJ) or a bond of the rounding (POST_BOND)
+__global__ void __launch_bounds__(kThreads) k_post(const DevProb P, const Stage S) {
+  extern __shared__ __align__(16) double sm[];
+  if (S.post == POST_SMALL_PROJ)
+    post_small_proj(P, sm);
+  else if (S.post == POST_BOND)
+    post_bond(P, S.post_k, sm);
 }
 
 // ---- warp-per-slice forms (ranks <= 8, so q <= 16) --------------------------
@@ -1792,7 +1801,8 @@ struct Plan {
   std::vector<Stage> psi;        // k = d-1 .. 1
   std::vector<Stage> sweep;      // bond k (+ map of core k-1), then the final maps
   std::vector<Stage> metric[2];  // Gram sweep of ||A - B||^2, which = 0 truth, 1 previous
-  size_t smem_stage = 0;
+  size_t smem_stage = 0;       // block-per-slice stages (slice jobs, maps, reductions)
+  size_t smem_post = 0;        // k_post: the small projection or a bond
   size_t smem_b1 = 0;         // float-float k_build_B1: seven regions of rmax (rmax + 1) float pairs
   bool warp = false;          // warp-per-slice kernels (ranks <= 8)
   size_t smem_warp = 0;
@@ -1834,13 +1844,18 @@ inline double slice_work(int op, int ra, int rb, int qa, int qb, int k) {
 inline double map_work(int ra, int rb, int qa, int qb) { return (double)ra * qb * qa + (double)ra * rb * qb; }
 inline int nblocks_warp(int nk) { return std::max(1, std::min((nk + kWarpsW - 1) / kWarpsW, 256)); }
 
-int launch_stage(ttc_ctx* c, const Stage& S, size_t smem) {
+int launch_stage(ttc_ctx* c, const Stage& S, size_t smem, size_t smem_post) {
   int nb = 0;
   for (int i = 0; i < S.nmap; ++i) nb += S.map_nb[i];
   for (int j = 0; j < S.njob; ++j) nb += S.job[j].nb;
   k_stage<<<nb, kThreads, smem, c->stream>>>(c->hp, S);
   TTC_CUDA(cudaGetLastError());
   c->nlaunch += 1;
+  if (S.post == POST_SMALL_PROJ || S.post == POST_BOND) {
+    k_post<<<1, kThreads, smem_post, c->stream>>>(c->hp, S);
+    TTC_CUDA(cudaGetLastError());
+    c->nlaunch += 1;
+  }
   return TTC_OK;
 }
 
@@ -1869,7 +1884,7 @@ int launch_stage_w(ttc_ctx* c, const Stage& S, size_t smem) {
 }
 
 int run_stage(ttc_ctx* c, const Plan& pl, const Stage& S) {
-  return pl.warp ? launch_stage_w(c, S, pl.smem_warp) : launch_stage(c, S, pl.smem_stage);
+  return pl.warp ? launch_stage_w(c, S, pl.smem_warp) : launch_stage(c, S, pl.smem_stage, pl.smem_post);
 }
 
 }  // namespace
@@ -2065,8 +2080,11 @@ int ttc_alloc_dense(ttc_ctx* c) {
   size_t bond_need = sizeof(double) * (size_t)(6 * qmax * (qmax + 1) + kThreads + 2 * qmax);
   // float-float slice jobs and maps of FP32 steps: four regions of q (q + 1) float pairs
   size_t ff_need = sizeof(float2) * (size_t)(4 * qmax * (qmax + 1));
-  pl.smem_stage = std::max(std::max(red_need, ff_need), std::max(proj_need, bond_need)) + 64;
-  pl.smem_warp = pl.warp ? std::max(pl.smem_stage, sizeof(double) * (size_t)kWarpsW * 3 * wscr_mat_host(P))
+  pl.smem_stage = std::max(red_need, ff_need) + 64;
+  pl.smem_post = std::max(proj_need, bond_need) + 64;
+  // the warp-per-slice kernels run the posts in their last block
+  pl.smem_warp = pl.warp ? std::max(std::max(pl.smem_stage, pl.smem_post),
+                                    sizeof(double) * (size_t)kWarpsW * 3 * wscr_mat_host(P))
                          : pl.smem_stage;
   pl.smem_b1 = sizeof(float2) * (size_t)(7 * rmax * (rmax + 1));
   {
@@ -2083,8 +2101,9 @@ int ttc_alloc_dense(ttc_ctx* c) {
                                     (int)(sizeof(float2) * 7 * TTC_MAXR * (TTC_MAXR + 1))));
       b1_granted[dev] = true;
     }
-    if (granted[dev] < pl.smem_warp) {
-      const int sz = (int)pl.smem_warp;   // >= smem_stage
+    if (granted[dev] < std::max(pl.smem_warp, pl.smem_post)) {
+      const int sz = (int)std::max(pl.smem_warp, pl.smem_post);   // >= smem_stage
+      TTC_CUDA(cudaFuncSetAttribute(k_post, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
       TTC_CUDA(cudaFuncSetAttribute(k_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
       TTC_CUDA(cudaFuncSetAttribute(k_stage_w<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
       TTC_CUDA(cudaFuncSetAttribute(k_stage_w<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
@@ -2096,7 +2115,7 @@ int ttc_alloc_dense(ttc_ctx* c) {
       TTC_CUDA(cudaFuncSetAttribute(k_stage_w_batch<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
       TTC_CUDA(cudaFuncSetAttribute(k_stage_w_batch<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
       TTC_CUDA(cudaFuncSetAttribute(k_build_C_w_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, sz));
-      granted[dev] = pl.smem_warp;
+      granted[dev] = std::max(pl.smem_warp, pl.smem_post);
     }
   }
   plan_of(c) = pl;
@@ -2347,7 +2366,7 @@ int ttc_launch_metric(ttc_ctx* c, int which) {
     J.red2 = red2;
     J.dst = P.off_mlam[2][k + 1];
     S.job[S.njob++] = J;
-    TTC_TRY(launch_stage(c, S, pl.smem_stage));
+    TTC_TRY(launch_stage(c, S, pl.smem_stage, 0));
   }
   return TTC_OK;
 }

@@ -830,7 +830,7 @@ __device__ __forceinline__ void sample_project(const DevProb& P, const int blk) 
 template <typename T, int RC, int MC>
 constexpr int min_blocks() {
   return sizeof(T) != 4 ? 1
-         : RC > 8 ? ((MC == PC_MIDDLE && RC <= 24) ? 2 : 1)
+         : RC > 8 ? (RC <= 24 ? 2 : 1)
          : (MC == PC_FIRST || MC == PC_LAST) ? (RC <= 6 ? 4 : 3)
          : (MC == PC_MIDDLE && RC <= 5) ? 2 : 1;
 }

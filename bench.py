@@ -623,7 +623,7 @@ def ttc_arm(args):
         line = {
             "metric": METRIC, "value": value, "unit": "Ω-entries/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 sampled pass + f64 dense stages", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32 sampled pass + float-float slice products + f64 factorizations", "data": "synthetic",
             "config": dict(HEADLINE if args.workload == "hyperspectral_like" else {"workload": args.workload},
                            batch=B, precision="mixed", l2=hb["l2"],
                            parallelism="replicas" if world > 1 else "single GPU"),

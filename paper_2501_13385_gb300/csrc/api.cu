@@ -409,6 +409,12 @@ int ttc_set_observations(ttc_ctx* c, int64_t N, const int32_t* idx, const double
     TTC_TRY(ttc_alloc(c, (void**)&P.tab64, sizeof(double) * cnt, true));
     TTC_TRY(ttc_alloc(c, (void**)&P.ztab32, sizeof(float) * cnt, true));
     TTC_TRY(ttc_alloc(c, (void**)&P.ztab64, sizeof(double) * cnt, true));
+    // rows whose coordinates lie outside the mode sizes stand for no entry:
+    // zero once here, never written by the per-step builds
+    TTC_CUDA(cudaMemsetAsync(P.tab32, 0, sizeof(float) * cnt, c->stream));
+    TTC_CUDA(cudaMemsetAsync(P.tab64, 0, sizeof(double) * cnt, c->stream));
+    TTC_CUDA(cudaMemsetAsync(P.ztab32, 0, sizeof(float) * cnt, c->stream));
+    TTC_CUDA(cudaMemsetAsync(P.ztab64, 0, sizeof(double) * cnt, c->stream));
   }
   c->have_obs = true;
   c->eps_set = false;

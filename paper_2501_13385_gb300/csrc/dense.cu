@@ -1568,9 +1568,10 @@ __device__ __forceinline__ void ztable_row_chain(const DevProb& P, int t, long l
     valid = valid && x < P.n[j];
     if (valid) tangent_times<T, R, RC>(P, j, x, lT, lZ);
   }
+  if (!valid) return;   // a row that stands for no entry: zeroed at allocation
   T* dst = ptab<T>(P, true) + g * R;
 #pragma unroll
-  for (int a = 0; a < R; ++a) dst[a] = (valid && a < RC && a < P.r[jt]) ? lZ[a < RC ? a : 0] : T(0);
+  for (int a = 0; a < R; ++a) dst[a] = (a < RC && a < P.r[jt]) ? lZ[a < RC ? a : 0] : T(0);
 }
 
 // The tangent companion of the prefix tables: row i of ztab holds l_Z over
@@ -1612,7 +1613,7 @@ __global__ void __launch_bounds__(128) k_build_ztables(const DevProb P) {
         sB[i] = B11[i];
       }
       __syncthreads();
-      const bool valid = x0 < P.n[0];
+      const bool valid = x0 < P.n[0];   // rows that stand for no entry stay as zeroed at allocation
       T lT[RC], lZ[RC];
       const T* S0 = pcore<T>(P, 0) + (long long)(valid ? x0 : 0) * R * R;
       const T* B10 = pb1<T>(P, 0) + (long long)(valid ? x0 : 0) * R * R;
@@ -1622,9 +1623,9 @@ __global__ void __launch_bounds__(128) k_build_ztables(const DevProb P) {
         lZ[a] = (valid && a < r1) ? B10[a] : T(0);
       }
       T* dst = ptab<T>(P, true) + g * R;
-      for (int b = 0; b < R; ++b) {
+      for (int b = 0; b < R && valid; ++b) {
         T z = T(0);
-        if (valid && b < r2) {
+        if (b < r2) {
 #pragma unroll
           for (int a = 0; a < RC; ++a) {
             if (a < r1) {

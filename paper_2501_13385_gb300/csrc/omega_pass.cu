@@ -25,7 +25,8 @@ __device__ __forceinline__ void store_row(double* dst, const double (&v)[R]) {
 }
 
 // one table row per thread: the chain of core slices it stands for (rows
-// whose coordinates are outside the mode sizes are written as zeros)
+// whose coordinates are outside the mode sizes stand for no entry: zeroed
+// once when the tables are allocated, not written here)
 template <typename T, int R>
 __device__ __forceinline__ void build_table_row(const DevProb& P, long long g) {
   int t = 0;
@@ -40,6 +41,7 @@ __device__ __forceinline__ void build_table_row(const DevProb& P, long long g) {
     xs[j] = (int)((row >> (P.cshift[j] - P.tab_shift[t])) & ((1u << P.cbits[j]) - 1u));
     valid = valid && xs[j] < P.n[j];
   }
+  if (!valid) return;
   T v[R];
   zero(v);
   v[0] = 1;
@@ -78,6 +80,7 @@ template <typename T, int R>
 __device__ __forceinline__ void prefix2_row(const DevProb& P, long long g, int x0, const T* sS) {
   const int r1 = P.r[1], r2 = P.r[2];
   const bool valid = x0 < P.n[0];
+  if (!valid) return;   // a row that stands for no entry is never read
   const T* S0 = core_ptr<T>(P, 0) + (long long)(valid ? x0 : 0) * R * R;   // a 1 x r_1 slice: row 0
   T l0[R], v[R];
 #pragma unroll

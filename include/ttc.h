@@ -250,6 +250,21 @@ int ttc_batch_create(ttc_batch** out, ttc_ctx* const* members, int count, void* 
 int ttc_batch_step(ttc_batch* b);
 /* Wait for all work enqueued by the batch. */
 int ttc_batch_sync(ttc_batch* b);
+/* Lanes (call before the first step; 1 = none): the members are split into
+ * `lanes` contiguous groups, each stepped by its own graph on its own
+ * stream.  A step forks the lanes from the batch's stream only when they
+ * are joined (after creation, ttc_batch_sync or ttc_batch_join), so between
+ * joins the lanes run ahead independently: one lane's sampled pass (bound
+ * by bandwidth and arithmetic across the GPU) overlaps another lane's dense
+ * chain (bound by the latency of its small factorizations).  Each member
+ * still computes what it computes alone (bitwise).  With lanes, the
+ * batch's stream sees the lanes' work only after ttc_batch_join, which
+ * enqueues a wait for all of it on that stream (no host wait); profiling
+ * then serialises the lanes (each profiled step waits on the host).
+ * Errors: TTC_EINVAL (lanes < 1 or more than the members, or after the
+ * first step), TTC_ECUDA. */
+int ttc_batch_set_lanes(ttc_batch* b, int lanes);
+int ttc_batch_join(ttc_batch* b);
 /* Profiling: the batched sampled-pass launch(es) of every step are bracketed
  * by events (graph event-record nodes), and so is the dense part of the step
  * (Lemma 3.5's projection, the step size and Algorithm 1's rounding of every

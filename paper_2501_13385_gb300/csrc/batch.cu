@@ -38,6 +38,12 @@ struct ttc_batch {
   long long kernels_per_step = 0;
   long long nlaunch = 0;
   bool prof = false;
+  // lanes: sub-batches over contiguous member groups, each on its own stream
+  std::vector<ttc_batch*> lanes;
+  std::vector<cudaEvent_t> lane_join;
+  cudaEvent_t lane_fork = nullptr;
+  bool forked = false;
+  bool stepped = false;
   cudaEvent_t ev_beg = nullptr, ev_end = nullptr;     // the pass
   cudaEvent_t ev_dbeg = nullptr, ev_dend = nullptr;   // the dense part
   double prof_ms = 0.0, prof_dense_ms = 0.0;
@@ -303,6 +309,20 @@ int ttc_batch_create(ttc_batch** out, ttc_ctx* const* members, int count, void* 
 
 int ttc_batch_step(ttc_batch* b) {
   if (!b) return TTC_EINVAL;
+  b->stepped = true;
+  if (!b->lanes.empty()) {
+    if (!b->forked) {   // the lanes start after the work already on the batch's stream
+      TTC_CUDA(cudaEventRecord(b->lane_fork, b->stream));
+      for (auto* l : b->lanes) TTC_CUDA(cudaStreamWaitEvent(l->stream, b->lane_fork, 0));
+      b->forked = true;
+    }
+    for (auto* l : b->lanes) {
+      const long long n0 = l->nlaunch;
+      TTC_TRY(ttc_batch_step(l));
+      b->nlaunch += l->nlaunch - n0;
+    }
+    return TTC_OK;
+  }
   bool stale = (b->exec == nullptr);
   for (size_t i = 0; i < b->members.size() && !stale; ++i)
     stale = (b->members[i]->cur_prec * 2 + b->members[i]->hp.steepest != b->prec_at_capture[i]);
@@ -332,12 +352,60 @@ int ttc_batch_step(ttc_batch* b) {
 
 int ttc_batch_sync(ttc_batch* b) {
   if (!b) return TTC_EINVAL;
+  for (auto* l : b->lanes) TTC_TRY(ttc_batch_sync(l));
+  b->forked = false;
   TTC_CUDA(cudaStreamSynchronize(b->stream));
+  return TTC_OK;
+}
+
+int ttc_batch_join(ttc_batch* b) {
+  if (!b) return TTC_EINVAL;
+  for (size_t i = 0; i < b->lanes.size(); ++i) {
+    TTC_CUDA(cudaEventRecord(b->lane_join[i], b->lanes[i]->stream));
+    TTC_CUDA(cudaStreamWaitEvent(b->stream, b->lane_join[i], 0));
+  }
+  b->forked = false;
+  return TTC_OK;
+}
+
+int ttc_batch_set_lanes(ttc_batch* b, int lanes) {
+  if (!b || lanes < 1 || lanes > (int)b->members.size() || b->stepped) return TTC_EINVAL;
+  if (lanes == 1 || !b->lanes.empty()) return lanes == 1 && b->lanes.empty() ? TTC_OK : TTC_EINVAL;
+  const int cnt = (int)b->members.size();
+  cudaError_t e = cudaEventCreateWithFlags(&b->lane_fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    ttc_record_cuda_error(e);
+    return TTC_ECUDA;
+  }
+  for (int l = 0; l < lanes; ++l) {
+    const int lo = (int)((long long)cnt * l / lanes), hi = (int)((long long)cnt * (l + 1) / lanes);
+    ttc_batch* sub = nullptr;
+    int s = ttc_batch_create(&sub, b->members.data() + lo, hi - lo, nullptr);   // own stream
+    cudaEvent_t ev = nullptr;
+    if (s == TTC_OK) {
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        ttc_record_cuda_error(e);
+        s = TTC_ECUDA;
+      }
+    }
+    if (s != TTC_OK) {
+      if (sub) ttc_batch_destroy(sub);
+      for (auto* x : b->lanes) ttc_batch_destroy(x);
+      for (auto x : b->lane_join) cudaEventDestroy(x);
+      b->lanes.clear();
+      b->lane_join.clear();
+      return s;
+    }
+    b->lanes.push_back(sub);
+    b->lane_join.push_back(ev);
+  }
   return TTC_OK;
 }
 
 int ttc_batch_profile_enable(ttc_batch* b, int on) {
   if (!b) return TTC_EINVAL;
+  for (auto* l : b->lanes) TTC_TRY(ttc_batch_profile_enable(l, on));
   if ((on != 0) != b->prof) {
     TTC_CUDA(cudaStreamSynchronize(b->stream));
     if (b->exec) {
@@ -349,8 +417,26 @@ int ttc_batch_profile_enable(ttc_batch* b, int on) {
   return TTC_OK;
 }
 
+// with lanes: the sums over the lanes (their profiled steps run one after
+// another, each waiting on the host)
+static int lanes_profile(ttc_batch* b, double* ms, int64_t* count, int reset, bool dense) {
+  double tot = 0.0;
+  int64_t n = 0;
+  for (auto* l : b->lanes) {
+    double v = 0.0;
+    int64_t c = 0;
+    TTC_TRY(dense ? ttc_batch_profile_read_dense(l, &v, &c, reset) : ttc_batch_profile_read(l, &v, &c, reset));
+    tot += v;
+    n = c;
+  }
+  if (ms) *ms = tot;
+  if (count) *count = n;
+  return TTC_OK;
+}
+
 int ttc_batch_profile_read(ttc_batch* b, double* ms, int64_t* count, int reset) {
   if (!b) return TTC_EINVAL;
+  if (!b->lanes.empty()) return lanes_profile(b, ms, count, reset, false);
   if (ms) *ms = b->prof_ms;
   if (count) *count = b->prof_count;
   if (reset) {
@@ -363,6 +449,7 @@ int ttc_batch_profile_read(ttc_batch* b, double* ms, int64_t* count, int reset) 
 
 int ttc_batch_profile_read_dense(ttc_batch* b, double* ms, int64_t* count, int reset) {
   if (!b) return TTC_EINVAL;
+  if (!b->lanes.empty()) return lanes_profile(b, ms, count, reset, true);
   if (ms) *ms = b->prof_dense_ms;
   if (count) *count = b->prof_count;
   if (reset) {
@@ -381,6 +468,9 @@ int ttc_batch_launch_count(ttc_batch* b, int64_t* launches) {
 
 void ttc_batch_destroy(ttc_batch* b) {
   if (!b) return;
+  for (auto* l : b->lanes) ttc_batch_destroy(l);   // each waits for its own stream
+  for (auto ev : b->lane_join) cudaEventDestroy(ev);
+  if (b->lane_fork) cudaEventDestroy(b->lane_fork);
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   free_groups(b);

@@ -88,7 +88,8 @@ EXPORTS = [
     "ttc_set_truth", "ttc_step", "ttc_solve", "ttc_relerr", "ttc_eval", "ttc_get_residual",
     "ttc_get_slice_energy", "ttc_get_scatter", "ttc_get_layout", "ttc_profile_enable", "ttc_profile_read",
     "ttc_device_bytes", "ttc_destroy", "ttc_strerror", "ttc_last_cuda_error", "ttc_launch_count",
-    "ttc_tt_dist2_static", "ttc_batch_create", "ttc_batch_step", "ttc_batch_sync", "ttc_batch_profile_enable",
+    "ttc_tt_dist2_static", "ttc_batch_create", "ttc_batch_step", "ttc_batch_sync", "ttc_batch_set_lanes",
+    "ttc_batch_join", "ttc_batch_profile_enable",
     "ttc_batch_profile_read", "ttc_batch_profile_read_dense", "ttc_batch_launch_count", "ttc_batch_destroy",
     "ttc_server_create", "ttc_submit", "ttc_poll", "ttc_server_stats", "ttc_server_destroy",
 ]
@@ -128,6 +129,8 @@ def lib():
         "ttc_destroy": (None, [vp]),
         "ttc_batch_create": (C.c_int, [C.POINTER(vp), C.POINTER(vp), C.c_int, vp]),
         "ttc_batch_step": (C.c_int, [vp]),
+        "ttc_batch_set_lanes": (C.c_int, [vp, C.c_int]),
+        "ttc_batch_join": (C.c_int, [vp]),
         "ttc_batch_sync": (C.c_int, [vp]),
         "ttc_batch_profile_enable": (C.c_int, [vp, C.c_int]),
         "ttc_batch_profile_read": (C.c_int, [vp, dp, i64p, C.c_int]),
@@ -329,18 +332,24 @@ class Batch:
     """Several contexts stepped together by one CUDA graph launch per iteration
     (ttc_batch_*).  Holds references to its members; close it before them."""
 
-    def __init__(self, members: Sequence[Context], stream: Optional[int] = None):
+    def __init__(self, members: Sequence[Context], stream: Optional[int] = None, lanes: int = 1):
         self.members = list(members)
         arr = (C.c_void_p * len(self.members))(*[m._h.value for m in self.members])
         self._h = C.c_void_p()
         _check(lib().ttc_batch_create(C.byref(self._h), arr, len(self.members),
                                       C.c_void_p(stream) if stream else None), "ttc_batch_create")
+        if lanes != 1:
+            _check(lib().ttc_batch_set_lanes(self._h, int(lanes)), "ttc_batch_set_lanes")
 
     def step(self):
         _check(lib().ttc_batch_step(self._h), "ttc_batch_step")
 
     def sync(self):
         _check(lib().ttc_batch_sync(self._h), "ttc_batch_sync")
+
+    def join(self):
+        """Make the batch's stream wait for the lanes' work (no host wait)."""
+        _check(lib().ttc_batch_join(self._h), "ttc_batch_join")
 
     def profile_enable(self, on: bool = True):
         _check(lib().ttc_batch_profile_enable(self._h, 1 if on else 0), "ttc_batch_profile_enable")

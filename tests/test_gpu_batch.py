@@ -57,6 +57,38 @@ def test_batch_members_bitwise_equal_to_alone():
         c.close()
 
 
+@pytest.mark.parametrize("lanes", [2, 3])
+def test_batch_lanes_bitwise_equal_to_alone(lanes):
+    # lanes: each group of members on its own graph and stream, running ahead
+    # between joins; every member still computes what it computes alone
+    steps = 4
+    alone = []
+    for i, (spec, prec) in enumerate(MEMBERS):
+        P, c = make(spec, prec, 300 + i)
+        for _ in range(steps):
+            c.step()
+        alone.append(c.get_cores())
+        c.close()
+    ctxs = [make(spec, prec, 300 + i)[1] for i, (spec, prec) in enumerate(MEMBERS)]
+    with ttc.Batch(ctxs, lanes=lanes) as b:
+        for s in range(steps):
+            b.step()
+            if s == 1:
+                b.join()       # a join in the middle: the next step forks the lanes again
+        b.profile_enable(True)
+        b.profile_enable(False)
+        b.sync()
+        assert b.launch_count() > 0
+        with pytest.raises(ttc.TTCError):
+            lib_lanes = ttc.lib().ttc_batch_set_lanes(b._h, 2)   # after the first step
+            ttc._check(lib_lanes, "ttc_batch_set_lanes")
+    for c, ref in zip(ctxs, alone):
+        got = c.get_cores()
+        for a, r in zip(got, ref):
+            assert np.array_equal(a, r)
+        c.close()
+
+
 def test_batch_profile_and_member_reuse():
     specs = [MEMBERS[1], MEMBERS[3]]
     ctxs = [make(spec, prec, 200 + i)[1] for i, (spec, prec) in enumerate(specs)]
